@@ -1,0 +1,302 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by
+mathematics (closed forms, brute force, conservation laws, printed values).
+
+None of these tests touches the CUDA library.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0911_5631_gb300 import inputs
+from conftest import read_golden
+
+RC = 2.0 ** (1.0 / 6.0)
+
+
+# --------------------------------------------------------------------------
+# Pair term, Eq. (1) + soft-sphere shift (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+def test_pair_closed_forms():
+    # LJ crosses zero at r = sigma = 1, so u(1) is the shift alone; the
+    # force there is -u'(1) = 48 - 24 = 24.
+    fr, u = oracle.pair(1.0, 1.0)
+    assert u == 1.0
+    assert fr == 24.0
+    # The soft-sphere shift makes u continuous at r_c = 2^(1/6), the minimum
+    # of Eq. (1) (u_LJ = -1, force 0).
+    fr, u = oracle.pair(RC * RC, 1.0)
+    assert abs(u) < 1e-14 and abs(fr) < 1e-13
+    # Without the shift Eq. (1) at its minimum is -epsilon.
+    assert abs(oracle.pair(RC * RC, 0.0)[1] + 1.0) < 1e-14
+
+
+@pytest.mark.parametrize("r", [0.8, 0.9, 1.0, 1.05, 1.1])
+def test_pair_force_is_minus_gradient(r):
+    # fr * r must equal -du/dr; check against a central difference of u.
+    h = 1e-6
+    u_p = oracle.pair((r + h) ** 2, 1.0)[1]
+    u_m = oracle.pair((r - h) ** 2, 1.0)[1]
+    dudr = (u_p - u_m) / (2 * h)
+    fr = oracle.pair(r * r, 1.0)[0]
+    assert fr * r == pytest.approx(-dudr, rel=1e-7)
+    assert fr > 0  # repulsive everywhere below r_c
+
+
+def test_two_atoms_across_boundary():
+    L = np.array([6.0, 6.0, 6.0])
+    pos = np.array([[-3.0 + 0.45, 0.1, -0.2], [3.0 - 0.45, 0.1, -0.2]])
+    f, U, W = oracle.forces_brute(pos, L, RC, 1.0)
+    fr, u = oracle.pair(0.81, 1.0)
+    # atom 0's nearest image of atom 1 sits at x = -3.45, so atom 0 is pushed +x
+    assert f[0, 0] == pytest.approx(fr * 0.9, rel=1e-12)
+    assert f[1, 0] == pytest.approx(-fr * 0.9, rel=1e-12)
+    assert np.all(f[:, 1:] == 0)
+    assert U == pytest.approx(u, rel=1e-14)
+    assert W == pytest.approx(fr * 0.81, rel=1e-14)
+    G, ok = oracle.cell_grid(L, RC + 0.3)
+    assert ok
+    fc, Uc, Wc = oracle.forces_cells(pos, L, G, RC, 1.0)
+    assert np.allclose(fc, f, rtol=0, atol=1e-13)
+
+
+def test_three_collinear_atoms():
+    # middle atom between two neighbours at 0.95 and 1.05: the net force on it
+    # is the difference of the two pair forces along x.
+    L = np.array([10.0, 10.0, 10.0])
+    pos = np.array([[-0.95, 0.0, 0.0], [0.0, 0.0, 0.0], [1.05, 0.0, 0.0]])
+    f, U, W = oracle.forces_brute(pos, L, RC, 1.0)
+    fa, ua = oracle.pair(0.95 ** 2, 1.0)
+    fb, ub = oracle.pair(1.05 ** 2, 1.0)
+    assert f[1, 0] == pytest.approx(fa * 0.95 - fb * 1.05, rel=1e-12)
+    assert f[0, 0] == pytest.approx(-fa * 0.95, rel=1e-12)
+    assert f[2, 0] == pytest.approx(fb * 1.05, rel=1e-12)
+    assert U == pytest.approx(ua + ub, rel=1e-14)  # 1.9 apart: outside r_c
+
+
+# --------------------------------------------------------------------------
+# Region, wrap and cells (Sec. 2.1, 2.2, 4.2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("row", read_golden("paper_cell_counts.txt"))
+def test_cell_counts_tables_1_and_5(row):
+    pot, ne, rho, rc, delta, nc, src = row
+    ne, rho, rc, delta, nc = int(ne), float(rho), float(rc), float(delta), int(nc)
+    L = ne / rho ** (1.0 / 3.0)
+    G, ok = oracle.cell_grid([L, L, L], rc + delta, even=True)
+    assert ok
+    assert int(np.prod(G)) == nc, (pot, ne, delta, src)
+    # the plain formula never gives fewer cells than the printed count
+    Gp, _ = oracle.cell_grid([L, L, L], rc + delta, even=False)
+    assert np.all(Gp >= G) and np.all(Gp - G <= 1)
+
+
+def test_wrap_known_values():
+    L = np.array([4.0, 5.0, 6.0])
+    pos = np.array([[2.0, -2.5, 0.0], [-2.1, 2.6, 9.5], [6.3, -7.4, -3.0]])
+    w = oracle.wrap(pos, L)
+    assert np.allclose(w, [[-2.0, -2.5, 0.0], [1.9, -2.4, -2.5], [-1.7, -2.4, -3.0]], atol=1e-13)
+    assert np.all(w >= -L / 2) and np.all(w < L / 2)
+
+
+def test_cell_of_known_cells():
+    L = np.array([7.5, 9.0, 6.0])
+    G = np.array([5, 6, 4])
+    w = L / G
+    rng = np.random.default_rng(0)
+    cx, cy, cz = (rng.integers(0, g, 200) for g in G)
+    frac = rng.uniform(0.05, 0.95, (200, 3))
+    pos = (np.stack([cx, cy, cz], 1) + frac) * w - L / 2
+    cell = oracle.cell_of(pos, L, G)
+    assert np.array_equal(cell, (cz * G[1] + cy) * G[0] + cx)
+    # faces: the lower face belongs to cell 0, the upper face wraps to cell 0
+    edge = np.array([[-L[0] / 2, -L[1] / 2, -L[2] / 2], [L[0] / 2, 0.0, 0.0]])
+    c = oracle.cell_of(edge, L, G)
+    assert c[0] == 0
+    assert c[1] % G[0] == 0
+
+
+# --------------------------------------------------------------------------
+# Pair enumeration: half-shell cell lists == O(N^2) definition (Sec. 2.2)
+# --------------------------------------------------------------------------
+
+def _as_set(pairs):
+    return set(map(tuple, np.asarray(pairs).tolist()))
+
+
+def _assert_same_pairs(a, b, pos, L, rcut, tol=1e-12):
+    sa, sb = _as_set(a), _as_set(b)
+    for (i, j) in sa ^ sb:  # only pairs within rounding of the cutoff may differ
+        assert abs(oracle.pair_r2(pos, L, i, j) - rcut * rcut) < tol, (i, j)
+
+
+CASES = [
+    # (n, rho, aspect, skin, seed, jitter)
+    (108, 0.8, (1, 1, 1), 0.4, 1, 0.2),
+    (256, 0.8, (1, 1, 1), 0.0, 2, 0.25),
+    (500, 1.0, (1, 1, 1), 0.4, 3, 0.1),
+    (864, 0.6, (1.0, 1.3, 0.8), 0.3, 4, 0.3),
+    (1372, 0.8, (1, 1, 1), 0.6, 5, 0.2),
+    (333, 0.8, (0.7, 1.0, 1.4), 0.4, 6, 0.35),  # ragged count, odd box
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_cell_pairs_match_brute_force(case):
+    n, rho, aspect, skin, seed, jit = case
+    pos, vel, L = inputs.wca_state(n, rho, 1.0, seed, jitter_amp=jit, aspect=aspect)
+    pos = oracle.wrap(pos, L)
+    rn = RC + skin
+    G, ok = oracle.cell_grid(L, rn)
+    if not ok:
+        pytest.skip("box too small for a 3-cell grid")
+    pc = oracle.pairs_cells(pos, L, G, rn)
+    pb = oracle.pairs_brute(pos, L, rn)
+    assert len(pc) > n  # a dense fluid: several neighbours per atom
+    _assert_same_pairs(pc, pb, pos, L, rn)
+    # every pair appears once
+    assert len(_as_set(pc)) == len(pc)
+
+
+def test_smallest_grid_g3():
+    # L just above 3 r_n: each cell's 27-neighbourhood covers the whole box
+    rn = RC + 0.4
+    L = np.array([3.05 * rn] * 3)
+    n = 110
+    pos = inputs.jitter(inputs.fcc_positions(n, L), 0.3, 11)
+    pos = oracle.wrap(pos, L)
+    G, ok = oracle.cell_grid(L, rn)
+    assert ok and tuple(G) == (3, 3, 3)
+    _assert_same_pairs(oracle.pairs_cells(pos, L, G, rn), oracle.pairs_brute(pos, L, rn), pos, L, rn)
+
+
+def test_neighbors_of_matches_pair_set():
+    pos, vel, L = inputs.wca_state(500, 0.8, 1.0, 7, jitter_amp=0.2)
+    pos = oracle.wrap(pos, L)
+    rn = RC + 0.4
+    pb = oracle.pairs_brute(pos, L, rn)
+    for i in [0, 17, 250, 499]:
+        expect = sorted(set(pb[pb[:, 0] == i, 1].tolist()) | set(pb[pb[:, 1] == i, 0].tolist()))
+        assert oracle.neighbors_of(pos, L, rn, i).tolist() == expect
+
+
+# --------------------------------------------------------------------------
+# Forces, energy, virial
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", CASES[:4])
+def test_cell_forces_match_brute_force(case):
+    n, rho, aspect, skin, seed, jit = case
+    pos, vel, L = inputs.wca_state(n, rho, 1.0, seed, jitter_amp=jit, aspect=aspect)
+    pos = oracle.wrap(pos, L)
+    G, ok = oracle.cell_grid(L, RC)
+    fb, Ub, Wb = oracle.forces_brute(pos, L, RC, 1.0)
+    fc, Uc, Wc = oracle.forces_cells(pos, L, G, RC, 1.0)
+    scale = np.abs(fb).max()
+    assert scale > 1.0
+    assert np.abs(fc - fb).max() <= 1e-12 * scale
+    assert Uc == pytest.approx(Ub, rel=1e-12)
+    assert Wc == pytest.approx(Wb, rel=1e-12)
+    # Newton's third law holds in the result
+    assert np.abs(fb.sum(axis=0)).max() <= 1e-12 * scale * n
+
+
+def test_sampled_forces_and_full_list_energy():
+    pos, vel, L = inputs.wca_state(500, 0.8, 1.0, 9, jitter_amp=0.25)
+    pos = oracle.wrap(pos, L)
+    fb, Ub, Wb = oracle.forces_brute(pos, L, RC, 1.0)
+    idx = np.arange(500)
+    fs, us = oracle.forces_sampled(pos, L, RC, 1.0, idx)
+    assert np.allclose(fs, fb, rtol=0, atol=1e-11 * np.abs(fb).max())
+    # the per-atom sums over all partners count each pair twice (Sec. 2.3)
+    assert us.sum() == pytest.approx(2 * Ub, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# The MD loop (Sec. 2.1)
+# --------------------------------------------------------------------------
+
+def _fluid(n=500, rho=0.8, T=1.0, seed=21, jit=0.2):
+    pos, vel, L = inputs.wca_state(n, rho, T, seed, jitter_amp=jit)
+    return oracle.wrap(pos, L), vel, L
+
+
+def test_momentum_conserved():
+    pos, vel, L = _fluid()
+    out = oracle.run(pos, vel, L, RC, 0.4, 0.005, 300)
+    assert np.abs(vel.sum(axis=0)).max() < 1e-12
+    assert np.abs(out["vel"].sum(axis=0)).max() < 1e-10
+    assert out["nrebuild"] > 3
+
+
+def test_time_reversible():
+    pos, vel, L = _fluid()
+    a = oracle.run(pos, vel, L, RC, 0.4, 0.005, 200)
+    b = oracle.run(a["pos"], -a["vel"], L, RC, 0.4, 0.005, 200)
+    d = b["pos"] - pos
+    d -= L * np.round(d / L)
+    assert np.abs(d).max() < 1e-9
+    assert np.abs(b["vel"] + vel).max() < 1e-9
+
+
+def test_skin_does_not_change_the_trajectory():
+    # Any valid neighbour list gives the same forces; the delta/2 rule must
+    # rebuild early enough.  Compare against rebuilding every step.
+    pos, vel, L = _fluid(T=2.0)
+    a = oracle.run(pos, vel, L, RC, 0.0, 0.005, 100)
+    b = oracle.run(pos, vel, L, RC, 0.5, 0.005, 100)
+    d = b["pos"] - a["pos"]
+    d -= L * np.round(d / L)
+    assert b["nrebuild"] >= 2 and a["nrebuild"] == 100
+    assert np.abs(d).max() < 1e-10
+    assert np.abs(b["vel"] - a["vel"]).max() < 1e-9
+
+
+def test_energy_error_scales_as_dt_squared():
+    pos, vel, L = _fluid(n=256, seed=5)
+    amp = []
+    for dt in (0.004, 0.002):
+        steps = int(round(0.8 / dt))
+        out = oracle.run(pos, vel, L, RC, 0.4, dt, steps)
+        e = out["ke"] + out["pe"]
+        amp.append(np.sqrt(np.mean((e - e.mean()) ** 2)))
+    assert 3.0 < amp[0] / amp[1] < 5.2
+
+
+def _equilibrated(n, skin, seed, steps_eq=1000):
+    pos, vel, L = inputs.wca_state(n, 0.8, 1.0, seed)
+    pos = oracle.wrap(pos, L)
+    # paper's protocol: rescale every 20 steps during 500 steps
+    eq = oracle.run(pos, vel, L, RC, skin, 0.005, steps_eq, rescale_every=20, rescale_until=500,
+                    record=False)
+    return eq["pos"], eq["vel"], L
+
+
+@pytest.mark.parametrize("delta,expect", [(float(r[1].split("=")[1]), float(r[2]))
+                                          for r in read_golden("paper_sp_statistics.txt")
+                                          if r[0] == "np_per_atom" and r[1] in ("delta=0.4", "delta=0.6")])
+def test_neighbour_count_table5(delta, expect):
+    # N_p/N_a of Table 5 for an equilibrated rho = 0.8, T = 1 fluid: the full
+    # list has twice as many entries as the half list built here.
+    n = 4000
+    pos, vel, L = _equilibrated(n, delta, 31)
+    out = oracle.run(pos, vel, L, RC, delta, 0.005, 400, record=False)
+    builds = out["nrebuild"] + 1
+    per_atom = 2.0 * out["npairs_sum"] / builds / n
+    assert per_atom == pytest.approx(expect, rel=0.01)
+
+
+def test_equation_of_state_table4():
+    # Table 4: <e_tot> - <e_kin> = <e_pot> per atom at T = 1, rho = 0.8.
+    g = {r[0]: float(r[2]) for r in read_golden("paper_sp_statistics.txt") if r[0] in ("e_tot", "e_kin")}
+    epot_paper = g["e_tot"] - g["e_kin"]
+    n = 2048
+    pos, vel, L = _equilibrated(n, 0.4, 41)
+    # keep T at 1 while averaging so the comparison is at the paper's T
+    out = oracle.run(pos, vel, L, RC, 0.4, 0.005, 2000, rescale_every=20, rescale_until=10 ** 9)
+    epot = out["pe"][1:].mean() / n
+    ekin = out["ke"][1:].mean() / n
+    assert ekin == pytest.approx(1.5, abs=0.01)
+    assert epot == pytest.approx(epot_paper, abs=0.004)
