@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the soft-sphere MD hot path on GB300.
+
+Workload (default): 1,048,576 WCA atoms (FCC 64^3 x 4), rho = 0.8, T = 1.0,
+dt = 0.005, neighbour list with skin 0.4, reorder every 100 steps.  The
+state is equilibrated untimed, then every benchmark "step" advances 100 MD
+steps (one reorder interval: about ten list rebuilds and one reorder) through
+md_step.  The metric is atom-steps per second of the mixed-precision form;
+the plain FP64 GPU form is timed on the same workload beside it.
+
+One JSON line is printed by rank 0.  Under torchrun every rank runs an
+independent replica on its own GPU (the path has no exchange step), timing is
+the max over ranks and ``value`` sums the atoms of all ranks.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead
+(a bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0911_5631_gb300 import inputs  # noqa: E402
+
+METRIC = "atom-steps/s at 1M WCA atoms (mixed vs FP64 GPU form); ensemble p50/p99 latency"
+UNIT = "atom-steps/s"
+RC = 2.0 ** (1.0 / 6.0)
+DT = 0.005
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="wca_fcc64_n1m")
+    ap.add_argument("--chunk", type=int, default=100, help="MD steps per benchmark step")
+    ap.add_argument("--equil", type=int, default=1000, help="untimed equilibration MD steps")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eager", action="store_true", help="stream launches instead of graphs")
+    ap.add_argument("--profile-steps", type=int, default=2,
+                    help="benchmark steps run with per-kernel CUDA events for the roofline")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("md_kernels.cuh", "md_common.cuh"):
+        with open(os.path.join(ROOT, "paper_0911_5631_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, precision):
+    """Per-launch DRAM bytes of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get("%s/%s" % (workload, precision))
+    if not e or e.get("kernel_source") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def run_reference(args):
+    """Times the FP64 CPU oracle on the host cores."""
+    import oracle
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cfg = inputs.WORKLOADS[args.workload]
+    n = cfg["n"]
+    pos, vel, L = inputs.wca_state(n, cfg["rho"], cfg["T"], cfg["seed"])
+    pos = oracle.wrap(pos, L)
+    sample = 4  # MD steps per benchmark step, from the lattice start
+    for _ in range(args.warmup):
+        oracle.run(pos, vel, L, RC, cfg["skin"], DT, sample, record=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(pos, vel, L, RC, cfg["skin"], DT, sample, record=False)
+    t = time.perf_counter() - t0
+    value = n * sample * args.steps / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": args.workload, "n_atoms": n, "rho": cfg["rho"],
+                                        "T": cfg["T"], "skin": cfg["skin"],
+                                        "md_steps_per_bench_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d MD steps of the %d-atom workload from its lattice start per "
+                                   "benchmark step, single-threaded C oracle" % (sample, n)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(pos, vel, L, cfg, seconds=12.0):
+    """The oracle as it stands, single-threaded, on a bounded sample."""
+    import oracle
+    n = pos.shape[0]
+    p = oracle.wrap(pos, L)
+    t0 = time.perf_counter()
+    oracle.run(p, vel, L, RC, cfg["skin"], DT, 2, record=False)
+    t1 = time.perf_counter() - t0
+    steps = int(max(4, min(400, seconds / max(t1 / 2, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.run(p, vel, L, RC, cfg["skin"], DT, steps, record=False)
+    t = time.perf_counter() - t0
+    return {"value": n * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d MD steps of the %d-atom equilibrated state (includes the initial list build), "
+                      "single-threaded C oracle, %.1f s" % (steps, n, t)}
+
+
+def run_ours(args):
+    import torch
+    import paper_0911_5631_gb300 as md
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    cfg = inputs.WORKLOADS[args.workload]
+    n = cfg["n"]
+    pos, vel, L = inputs.wca_state(n, cfg["rho"], cfg["T"], cfg["seed"] + 1000 * rank)
+    stream = torch.cuda.Stream()
+
+    def make(precision):
+        s = md.Simulation(L, n, RC, cfg["skin"], DT, precision=precision, reorder_interval=100,
+                          use_graphs=not args.eager, stream=stream.cuda_stream, device=local)
+        s.set_state(pos, vel)
+        return s
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def timed(sim, k):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            sim.step(args.chunk)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        barrier()
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms
+
+    # ---- mixed form: the headline ----
+    sim = make("mixed")
+    sim.step(args.equil)
+    eq_pos, eq_vel = sim.get_state()
+    for _ in range(args.warmup):
+        sim.step(args.chunk)
+    st0 = sim.kernel_stats()
+    m0 = sim.measure()
+    clocks = Clocks(local)
+    clocks.start()
+    ms = timed(sim, args.steps)
+    clk = clocks.stop()
+    m1 = sim.measure()
+    st1 = sim.kernel_stats()
+    atom_steps = n * args.chunk * args.steps * ws
+    value = atom_steps / (ms / 1e3)
+    launches = st1["launches"] - st0["launches"]
+
+    # ---- roofline of the force + integrate kernel (event-timed launches) ----
+    sim.set_profiling(True)
+    p0 = sim.kernel_stats()
+    for _ in range(args.profile_steps):
+        sim.step(args.chunk)
+    p1 = sim.kernel_stats()
+    sim.set_profiling(False)
+    kms = p1["step_kernel_ms"] - p0["step_kernel_ms"]
+    kl = p1["step_kernel_launches"] - p0["step_kernel_launches"]
+    kbytes = p1["step_kernel_bytes"] - p0["step_kernel_bytes"]
+    peak, peak_kind = measured_peaks()
+    achieved = (kbytes / kl) / (kms / kl / 1e3) / 1e9 if kl and kms > 0 else None
+    traffic = ncu_traffic(args.workload, "mixed")
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_kind": peak_kind, "kernel": "k_step (force + integrate, mixed)",
+                "kernel_ms_per_launch": kms / kl if kl else None,
+                "algorithmic_bytes_per_launch": kbytes / kl if kl else None}
+    list_entries = m1["list_entries"]
+    rebuilds = m1["rebuilds"] - m0["rebuilds"]
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region ----
+    e2e = None
+    if not args.no_e2e:
+        hp = torch.from_numpy(eq_pos.copy()).pin_memory()
+        hv = torch.from_numpy(eq_vel.copy()).pin_memory()
+        op = torch.empty_like(hp).pin_memory()
+        ov = torch.empty_like(hv).pin_memory()
+        lib = md.lib()
+        k_e2e = max(2, args.steps // 4)
+
+        def e2e_step():
+            md._check(lib.md_set_state(sim.h, hp.data_ptr(), hv.data_ptr()), sim.h)
+            sim.step(args.chunk)
+            md._check(lib.md_get_state(sim.h, op.data_ptr(), ov.data_ptr()), sim.h)
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_step()
+        barrier()
+        t = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([t], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        e2e = {"value": n * args.chunk * k_e2e * ws / t, "unit": UNIT,
+               "h2d_bytes_per_step": int(hp.numel() * 8 + hv.numel() * 8),
+               "d2h_bytes_per_step": int(op.numel() * 8 + ov.numel() * 8),
+               "steps": k_e2e, "what": "md_set_state from pinned host memory, md_step(%d), "
+                                        "md_get_state to pinned host memory" % args.chunk}
+    sim.close()
+
+    # ---- plain FP64 GPU form on the same workload ----
+    fp64 = None
+    if not args.no_fp64:
+        s64 = make("fp64")
+        s64.set_state(eq_pos, eq_vel)
+        k64 = max(2, args.steps // 4)
+        for _ in range(max(1, args.warmup // 2)):
+            s64.step(args.chunk)
+        ms64 = timed(s64, k64)
+        s64.set_profiling(True)
+        q0 = s64.kernel_stats()
+        s64.step(args.chunk)
+        q1 = s64.kernel_stats()
+        s64.close()
+        v64 = n * args.chunk * k64 * ws / (ms64 / 1e3)
+        kms64 = q1["step_kernel_ms"] - q0["step_kernel_ms"]
+        kl64 = q1["step_kernel_launches"] - q0["step_kernel_launches"]
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                "step_kernel_ms_per_launch": kms64 / kl64 if kl64 else None,
+                "mixed_over_fp64": value / v64}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(eq_pos, eq_vel, L, cfg)
+
+    if rank == 0:
+        ws_bytes = n * (12 + 24 + 12 + 32 + 4) + list_entries * 4 * 1.3
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair / f64 position / int64 force sum",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "n_atoms": n, "rho": cfg["rho"], "T": cfg["T"],
+                       "skin": cfg["skin"], "dt": DT, "reorder_interval": 100, "precision": "mixed",
+                       "md_steps_per_bench_step": args.chunk, "equilibration_steps": args.equil,
+                       "graphs": not args.eager,
+                       "l2": "no flush: per-step working set %.0f MB > 129 MB L2" % (ws_bytes / 2 ** 20),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "gpu_launches": int(launches),
+            "rebuilds_in_timed_region": int(rebuilds),
+            "neighbours_per_atom": list_entries / n,
+            "roofline": roofline,
+            "fp64_form": fp64,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

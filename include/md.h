@@ -1,0 +1,223 @@
+/*
+ * md.h -- C ABI of the GB300 soft-sphere molecular-dynamics library (libmd).
+ *
+ * The library runs the per-step short-range hot path of Rapaport, "Enhanced
+ * molecular dynamics performance with a programmable graphics processor"
+ * (arXiv 0911.5631) on one NVIDIA GB300 (sm_103a):
+ *
+ *   cell binning (Sec. 2.2, Sec. 4.2) -> neighbour list with a shell of
+ *   thickness delta (Sec. 2.1, Sec. 2.4) -> pair forces, potential energy
+ *   and virial from Eq. (1) (Sec. 2.4) -> velocity-Verlet ("leapfrog")
+ *   integration with the delta/2 rebuild rule (Sec. 2.1, steps (a)-(e)),
+ *   with periodic cell-order reordering of the atoms (Sec. 2.5).
+ *
+ * Units are reduced MD units: sigma = epsilon = m = 1.  The region is a
+ * rectangular periodic box centred at the origin.
+ *
+ * Conventions for every call:
+ *   - Return value: MD_OK (0) or a negative MD_E* code.  md_last_error()
+ *     gives a human-readable message for the handle's most recent failure.
+ *   - Host arrays are caller owned; the library copies from/to them and
+ *     never keeps a pointer.  "_device" variants take device pointers in the
+ *     same layout (for example PyTorch CUDA tensors); the caller must keep
+ *     them valid until the call returns.
+ *   - Atom arrays are N x 3 row-major doubles (x, y, z per atom) in the
+ *     caller's atom order ("user order"); the library's internal reordering
+ *     is invisible through this interface.
+ *   - A handle is not thread safe; distinct handles may be used from
+ *     distinct host threads.
+ *   - All work is ordered on the handle's CUDA stream.  Calls that return
+ *     data to the host synchronise that stream.
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define MD_OK          0
+#define MD_EINVAL     -1  /* bad argument (sizes, geometry, NULL pointer)       */
+#define MD_ENOMEM     -2  /* device or host allocation failed                    */
+#define MD_ECUDA      -3  /* a CUDA runtime call failed; see md_last_error      */
+#define MD_ESTATE     -4  /* call order violated (e.g. md_step before state)    */
+#define MD_EOVERFLOW  -5  /* neighbour capacity exceeded and regrowth failed    */
+#define MD_EUNSTABLE  -6  /* non-finite coordinates, an atom moved more than a
+                             cell between rebuilds, or two atoms overlapped so
+                             closely that a pair force left the representable
+                             range                                            */
+#define MD_ENODEV     -7  /* no usable CUDA device                              */
+
+/* ---- precision forms -------------------------------------------------- */
+/* MD_PREC_MIXED: pair arithmetic in FP32 on cell-relative coordinates,
+ *   positions held as FP64 cell-relative offsets, per-atom force sums in
+ *   int64 fixed point (scale 2^32, independent of summation order),
+ *   velocities in FP32, FP64 in the position update and the reductions.
+ * MD_PREC_FP64: every arithmetic step in FP64. */
+#define MD_PREC_MIXED 0
+#define MD_PREC_FP64  1
+
+/* Optional parameters for md_create.  Fill with md_default_params() and
+ * change fields as needed. */
+typedef struct md_params {
+    int32_t precision;        /* MD_PREC_MIXED (default) or MD_PREC_FP64          */
+    int32_t reorder_interval; /* N_R of Sec. 5.4: atoms are put back into cell
+                                 order at the first rebuild at least this many
+                                 steps after the previous reorder; 0 = never.
+                                 Default 100.                                  */
+    int32_t cell_list_only;   /* 1: no neighbour list; every step re-bins the
+                                 atoms and takes forces straight from the 27
+                                 cells around each atom (Sec. 2.1, cells only).
+                                 Requires skin == 0.  Default 0.               */
+    int32_t even_cells;       /* 1: round each G_d down to an even number (the
+                                 rule behind the cell counts of Tables 1 and 5).
+                                 Default 0: G_d = floor(L_d / r_n) (Sec. 2.1). */
+    int32_t nbr_capacity;     /* initial neighbour slots per atom; 0 = estimate
+                                 from density and r_n.  Grown automatically.   */
+    int32_t use_graphs;       /* 1 (default): md_step replays CUDA graphs whose
+                                 rebuild branch is a device-side conditional
+                                 node; 0: plain stream launches (same results,
+                                 bit for bit).                                 */
+    int32_t device;           /* CUDA device ordinal; -1 (default) = current   */
+    int32_t reserved0;
+    double ushift;            /* constant added to Eq. (1) for r < r_c.  NaN
+                                 (default) = automatic: +1 (epsilon) when r_c is
+                                 2^(1/6) to 1e-12 relative (the soft-sphere
+                                 potential of Sec. 2.1), else 0.               */
+    void* stream;             /* cudaStream_t to run on; NULL (default) = a
+                                 stream created and owned by the handle.       */
+    int64_t reserved[6];
+} md_params;
+
+/* Geometry and resource plan, computed on the host without a GPU. */
+typedef struct md_plan_t {
+    int32_t G[3];             /* cells per dimension                            */
+    int32_t nbr_capacity;     /* initial neighbour slots per atom               */
+    int64_t n_cells;          /* G[0] * G[1] * G[2]                             */
+    double w[3];              /* cell widths L_d / G_d                          */
+    double rn;                /* r_c + skin                                     */
+    double ushift;            /* resolved potential shift                       */
+    int64_t device_bytes;     /* device memory the handle will allocate         */
+} md_plan_t;
+
+/* Thermodynamic measurement of the current state (integer time step). */
+typedef struct md_measure_t {
+    double ke;                /* sum 1/2 v^2                                    */
+    double pe;                /* sum over pairs of u(r) (with the shift)        */
+    double virial;            /* W = sum over pairs of r_ij . f_ij              */
+    double pressure;          /* (2 KE + W) / (3 V)                             */
+    double temperature;       /* 2 KE / (3 N)                                   */
+    double e_tot_per_atom;    /* (KE + PE) / N                                  */
+    double volume;            /* L_x L_y L_z                                    */
+    int64_t step;             /* steps taken since md_set_state                 */
+    int64_t rebuilds;         /* neighbour-list rebuilds since md_set_state     */
+    int64_t reorders;         /* cell-order reorders since md_set_state         */
+    int64_t list_entries;     /* current neighbour-list length (both directions,
+                                 the paper's N_p for the full list)            */
+    int32_t max_neighbors;    /* largest per-atom neighbour count at last build */
+    int32_t max_occupancy;    /* largest cell occupancy at last binning (N_l)   */
+    int32_t nbr_capacity;     /* current neighbour slots per atom               */
+    int32_t reserved;
+} md_measure_t;
+
+/* Launch/timing counters for profiling (see md_set_profiling). */
+typedef struct md_kernel_stats_t {
+    int64_t launches;         /* kernels launched by md_step so far             */
+    int64_t step_kernel_launches; /* force+integrate launches timed below       */
+    double step_kernel_ms;    /* summed CUDA-event time of those launches       */
+    int64_t step_kernel_atoms;/* atoms processed by them                        */
+    int64_t step_kernel_bytes;/* algorithmic bytes moved by them (see md_plan)  */
+} md_kernel_stats_t;
+
+typedef struct md_handle md_handle;
+
+/* Fills *p with the defaults documented in md_params. */
+void md_default_params(md_params* p);
+
+/* Plans geometry for a box of edges box[0..2], n atoms, cutoff rc, shell
+ * thickness skin (r_n = rc + skin, Sec. 2.1) and time step dt.  Returns
+ * MD_EINVAL when n <= 0, n >= 2^26, rc <= 0, skin < 0, dt <= 0, a box edge
+ * is not positive, some G_d < 3 (the 27-cell neighbourhood would alias), or
+ * cell_list_only is set with skin != 0.  p may be NULL.  Needs no GPU. */
+int md_plan(const double box[3], int64_t n, double rc, double skin, double dt,
+            const md_params* p, md_plan_t* out);
+
+/* Creates a simulation handle and allocates its device state (Sec. 2.1:
+ * region, cutoff, shell, time step).  Same argument checks as md_plan;
+ * MD_ENODEV / MD_ENOMEM / MD_ECUDA on device failure.  *out is NULL on
+ * error. */
+int md_create(const double box[3], int64_t n, double rc, double skin, double dt,
+              const md_params* p, md_handle** out);
+
+/* Loads positions and velocities (N x 3 each, user order, host memory).
+ * Positions are wrapped into the region; atoms are binned, the neighbour
+ * list is built and the forces of this state are computed, so the next
+ * md_step starts from true forces.  MD_EINVAL on NULL, MD_EUNSTABLE on
+ * non-finite input. */
+int md_set_state(md_handle* h, const double* pos, const double* vel);
+int md_set_state_device(md_handle* h, const double* pos, const double* vel);
+
+/* Advances nsteps velocity-Verlet steps (Sec. 2.1 (a)-(e)).  The neighbour
+ * list is rebuilt on the device whenever the largest displacement since the
+ * last build reaches skin/2 (every step in cell-list-only mode); atoms are
+ * reordered into cell order every reorder_interval steps at a rebuild.  If
+ * the list outgrows its capacity the library enlarges it and resumes from
+ * the step that overflowed.  Returns after the steps completed on the GPU.
+ * nsteps <= 0 is a no-op.  MD_ESTATE before md_set_state. */
+int md_step(md_handle* h, int64_t nsteps);
+
+/* Kinetic and potential energy, virial, pressure and counters of the
+ * current state (Sec. 2.5 global reductions, Sec. 4.3), reduced on the
+ * device in FP64 in a fixed order (run-to-run deterministic). */
+int md_measure(md_handle* h, md_measure_t* out);
+
+/* Current positions (wrapped into the region) and velocities, user order. */
+int md_get_state(md_handle* h, double* pos, double* vel);
+int md_get_state_device(md_handle* h, double* pos, double* vel);
+
+/* Forces on the atoms in the current state (N x 3, user order), as computed
+ * by the step kernel for the last completed step. */
+int md_get_forces(md_handle* h, double* f);
+
+/* Debug views for parity checks against a reference.
+ * md_debug_cells: cell index c = (c_z G_y + c_y) G_x + c_x of every atom as
+ *   last binned (N int32, user order).
+ * md_debug_neighbors: the unordered pairs of the current neighbour list in
+ *   user ids with i < j (2 x int32 per pair, up to capacity pairs written);
+ *   *count receives the number of pairs, *entries (may be NULL) the list
+ *   length counting both directions. */
+int md_debug_cells(md_handle* h, int32_t* cell);
+int md_debug_neighbors(md_handle* h, int64_t* count, int64_t* entries, int32_t* pairs,
+                       int64_t capacity);
+
+/* Plan of an existing handle (current capacity included). */
+int md_get_plan(md_handle* h, md_plan_t* out);
+
+/* Profiling: with on != 0, md_step runs without graphs and brackets every
+ * force+integrate kernel with CUDA events on the handle's stream; the
+ * totals accumulate in md_kernel_stats. */
+int md_set_profiling(md_handle* h, int on);
+int md_kernel_stats(md_handle* h, md_kernel_stats_t* out);
+
+/* Blocks until all work queued on the handle's stream is complete; returns
+ * any error the device recorded. */
+int md_sync(md_handle* h);
+
+/* Frees the handle and all its device memory.  NULL is a no-op. */
+void md_destroy(md_handle* h);
+
+/* Message for the handle's last failure ("" if none); h may be NULL for
+ * failures of md_create. */
+const char* md_last_error(const md_handle* h);
+
+/* Static description of an error code. */
+const char* md_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_H */

@@ -1,0 +1,932 @@
+// md_api.cu -- host runtime and C ABI of libmd (declared in include/md.h).
+//
+// A handle owns the device state of one simulation and a CUDA stream.  One
+// md_step call enqueues: the half kick + drift of the first step, then the
+// steps themselves.  With graphs enabled the steps run as replays of a
+// CUDA graph holding K (conditional rebuild, force + integrate) pairs; the
+// step kernel decides on the device whether the next rebuild branch runs
+// (cudaGraphSetConditional), so no host round trip sits inside the loop.
+// Without graphs the same kernels are launched one by one and the rebuild
+// kernels return early when the device flag is clear.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/md.h"
+#include "md_common.cuh"
+
+#include "md_table.h"
+
+namespace {
+
+using namespace md;
+
+thread_local std::string g_create_error;
+
+constexpr int kChunk = 32;  // steps per graph replay
+
+// Zeroed storage for cudaGraphNodeParams (its union has no default
+// constructor).
+struct NodeParams {
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    NodeParams() { std::memset(raw, 0, sizeof(raw)); }
+    cudaGraphNodeParams& get() { return *reinterpret_cast<cudaGraphNodeParams*>(raw); }
+};
+
+struct DevGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DevGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) changed = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DevGuard() {
+        if (changed && prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int resolve_plan(const double box[3], int64_t n, double rc, double skin, double dt, const md_params* p,
+                 md_plan_t* out, std::string* why) {
+    md_params d;
+    md_default_params(&d);
+    if (!p) p = &d;
+    auto fail = [&](const char* m) {
+        if (why) *why = m;
+        return MD_EINVAL;
+    };
+    if (!box || !out) return fail("NULL argument");
+    if (n <= 0) return fail("n must be positive");
+    if (n >= md::kMaxAtoms) return fail("n must be below 2^26 (neighbour entries carry a 6-bit cell code)");
+    if (!(rc > 0.0) || !std::isfinite(rc)) return fail("rc must be positive and finite");
+    if (!(skin >= 0.0) || !std::isfinite(skin)) return fail("skin must be non-negative and finite");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail("dt must be positive and finite");
+    if (p->precision != MD_PREC_MIXED && p->precision != MD_PREC_FP64) return fail("unknown precision");
+    if (p->cell_list_only && skin != 0.0) return fail("cell_list_only requires skin == 0");
+    if (p->reorder_interval < 0) return fail("reorder_interval must be >= 0");
+    if (p->nbr_capacity < 0) return fail("nbr_capacity must be >= 0");
+    std::memset(out, 0, sizeof(*out));
+    double rn = rc + skin;
+    int64_t nc = 1;
+    for (int k = 0; k < 3; k++) {
+        if (!(box[k] > 0.0) || !std::isfinite(box[k])) return fail("box edges must be positive and finite");
+        double g = std::floor(box[k] / rn);
+        if (g > 1e6) return fail("too many cells along one edge");
+        int G = (int)g;
+        if (p->even_cells) G -= G % 2;
+        if (G < 3) return fail("box edge below 3 r_n: the 27-cell neighbourhood would alias");
+        out->G[k] = G;
+        out->w[k] = box[k] / G;
+        nc *= G;
+    }
+    if (nc > (int64_t)1 << 30) return fail("too many cells");
+    out->n_cells = nc;
+    out->rn = rn;
+    if (std::isnan(p->ushift)) {
+        double wca = std::pow(2.0, 1.0 / 6.0);
+        out->ushift = std::fabs(rc - wca) <= 1e-12 * rc ? 1.0 : 0.0;
+    } else {
+        out->ushift = p->ushift;
+    }
+    int cap = 0;
+    if (!p->cell_list_only) {
+        if (p->nbr_capacity > 0) {
+            cap = p->nbr_capacity;
+        } else {
+            double rho = (double)n / (box[0] * box[1] * box[2]);
+            double nbar = 4.0 / 3.0 * M_PI * rn * rn * rn * rho;
+            cap = (int)std::ceil(nbar + 6.0 * std::sqrt(nbar) + 8.0);
+        }
+        cap = (cap + 3) & ~3;
+        if (cap < 8) cap = 8;
+        if (cap > 4096) cap = 4096;
+    }
+    out->nbr_capacity = cap;
+    // device bytes: see Sim::allocate
+    int64_t nb = (n + kBlock - 1) / kBlock;
+    int64_t real_b = p->precision == MD_PREC_FP64 ? 8 : 4;
+    int64_t pos4_b = p->precision == MD_PREC_FP64 ? 32 : 16;
+    int64_t per_atom = 3 * 4 /*cell perm rank*/ + 3 * real_b /*pb*/ + 24 /*o*/ + 3 * real_b /*v*/ +
+                       3 * real_b /*f*/ + 3 * pos4_b /*pA pB cand*/ + 8 + 3 * real_b + 24 + 3 * real_b /*scratch*/ +
+                       4 /*order*/ + 4 /*nn*/ + 48 /*io*/;
+    int64_t ncol = (n + 31) / 32 * 32;
+    out->device_bytes = per_atom * n + ncol * cap * 4 + (2 * nc + 1) * 4 + ((nc + kScanTile - 1) / kScanTile) * 4 +
+                        3 * nb * 8 + (int64_t)sizeof(Counters);
+    return MD_OK;
+}
+
+struct SimBase {
+    virtual ~SimBase() {}
+    virtual int set_state(const double* pos, const double* vel, bool device) = 0;
+    virtual int step(int64_t n) = 0;
+    virtual int measure(md_measure_t* out) = 0;
+    virtual int get_state(double* pos, double* vel, bool device) = 0;
+    virtual int get_forces(double* f) = 0;
+    virtual int debug_cells(int32_t* cell) = 0;
+    virtual int debug_neighbors(int64_t* count, int64_t* entries, int32_t* pairs, int64_t cap) = 0;
+    virtual int get_plan(md_plan_t* out) = 0;
+    virtual int set_profiling(int on) = 0;
+    virtual int kernel_stats(md_kernel_stats_t* out) = 0;
+    virtual int sync() = 0;
+    std::string err;
+    int device = 0;
+};
+
+#define MD_CUDA(call)                                                                    \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+            return e_ == cudaErrorMemoryAllocation ? MD_ENOMEM : MD_ECUDA;               \
+        }                                                                                \
+    } while (0)
+
+template <class P>
+struct Sim : SimBase {
+    using real = typename P::real;
+    using vel = typename P::vel;
+    using pos4 = typename P::pos4;
+
+    Args<P> a{};
+    KernelTable<P> kt{};
+    md_params prm{};
+    md_plan_t plan{};
+    double box[3] = {0, 0, 0};
+    double rc = 0, skin = 0, dt = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool have_state = false;
+    std::vector<void*> allocs;
+    int* nbr_alloc = nullptr;
+
+    struct Chunk {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t e = nullptr;
+        int K = 0;
+    };
+    Chunk big, one;
+    bool graphs_ok = false;
+
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    int64_t launches = 0;
+    int64_t graph_launches = 0;
+    int64_t steps_run = 0;
+    int64_t rebuilds_at_mark = 0;
+    double step_ms = 0.0;
+    int64_t step_launches = 0;
+    int64_t step_atoms = 0;
+    int64_t step_bytes = 0;
+
+    ~Sim() override {
+        DevGuard dg(device);
+        destroy_graphs();
+        for (auto e : ev) cudaEventDestroy(e);
+        for (void* p : allocs) cudaFree(p);
+        if (nbr_alloc) cudaFree(nbr_alloc);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+
+    template <class T>
+    int alloc(T** p, size_t count) {
+        void* q = nullptr;
+        MD_CUDA(cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16));
+        allocs.push_back(q);
+        *p = (T*)q;
+        return MD_OK;
+    }
+
+    int create(const double bx[3], int64_t n, double rc_, double skin_, double dt_, const md_params* p) {
+        md_default_params(&prm);
+        if (p) prm = *p;
+        for (int k = 0; k < 3; k++) box[k] = bx[k];
+        rc = rc_;
+        skin = skin_;
+        dt = dt_;
+        int rcode = resolve_plan(bx, n, rc, skin, dt, &prm, &plan, &err);
+        if (rcode) return rcode;
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+            cudaGetLastError();
+            err = "no CUDA device";
+            return MD_ENODEV;
+        }
+        if (prm.device >= ndev) {
+            err = "device ordinal out of range";
+            return MD_EINVAL;
+        }
+        if (prm.device >= 0) device = prm.device;
+        else MD_CUDA(cudaGetDevice(&device));
+        DevGuard dg(device);
+        if (prm.stream) {
+            stream = (cudaStream_t)prm.stream;
+        } else {
+            MD_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        kt = make_kernel_table<P>();
+        fill_scalars(n);
+        int r = allocate();
+        if (r) return r;
+        return MD_OK;
+    }
+
+    void fill_scalars(int64_t n) {
+        a.n = n;
+        a.cap = plan.nbr_capacity;
+        a.ncells = (int)plan.n_cells;
+        for (int k = 0; k < 3; k++) {
+            a.G[k] = plan.G[k];
+            a.L[k] = box[k];
+            a.hL[k] = 0.5 * box[k];
+            a.invL[k] = 1.0 / box[k];
+            a.invW[k] = (double)plan.G[k] / box[k];
+            a.w[k] = plan.w[k];
+            a.hw[k] = 0.5 * plan.w[k];
+            a.wf[k] = (float)plan.w[k];
+        }
+        a.ntiles = (int)((plan.n_cells + kScanTile - 1) / kScanTile);
+        a.nblocks = (int)((n + kBlock - 1) / kBlock);
+        a.cell_list_only = prm.cell_list_only;
+        a.reorder_interval = prm.reorder_interval;
+        a.dt = dt;
+        a.h = 0.5 * dt;
+        a.dtf = (float)dt;
+        a.hf = (float)(0.5 * dt);
+        a.rc2 = rc * rc;
+        a.rc2f = (float)a.rc2;
+        double rn = rc + skin;
+        a.rn2 = rn * rn;
+        double band = 1e-4 * a.rn2 + 1e-5;
+        a.rn2_lo = (float)(a.rn2 - band);
+        a.rn2_hi = (float)(a.rn2 + band);
+        a.ushift = plan.ushift;
+        a.ushiftf = (float)plan.ushift;
+        a.thr2 = 0.25 * skin * skin;
+        a.thr2f = (float)(a.thr2 * (1.0 - 1e-5));
+        a.close2 = 0.08;
+        a.close2f = 0.08f;
+    }
+
+    int allocate() {
+        int64_t n = a.n;
+        int r = 0;
+        auto chk = [&](int rr) { if (rr && !r) r = rr; };
+        chk(alloc(&a.cell, n)); chk(alloc(&a.perm, n)); chk(alloc(&a.rank, n));
+        chk(alloc(&a.pbx, n)); chk(alloc(&a.pby, n)); chk(alloc(&a.pbz, n));
+        chk(alloc(&a.ox, n)); chk(alloc(&a.oy, n)); chk(alloc(&a.oz, n));
+        chk(alloc(&a.vx, n)); chk(alloc(&a.vy, n)); chk(alloc(&a.vz, n));
+        chk(alloc(&a.fx, n)); chk(alloc(&a.fy, n)); chk(alloc(&a.fz, n));
+        chk(alloc(&a.pA, n)); chk(alloc(&a.pB, n)); chk(alloc(&a.cand, n));
+        chk(alloc(&a.s_cell, n)); chk(alloc(&a.s_perm, n));
+        chk(alloc(&a.s_pbx, n)); chk(alloc(&a.s_pby, n)); chk(alloc(&a.s_pbz, n));
+        chk(alloc(&a.s_ox, n)); chk(alloc(&a.s_oy, n)); chk(alloc(&a.s_oz, n));
+        chk(alloc(&a.s_vx, n)); chk(alloc(&a.s_vy, n)); chk(alloc(&a.s_vz, n));
+        chk(alloc(&a.count, a.ncells)); chk(alloc(&a.cell_start, (size_t)a.ncells + 1));
+        chk(alloc(&a.order, n)); chk(alloc(&a.tile_sum, a.ntiles));
+        chk(alloc(&a.nn, n));
+        chk(alloc(&a.part, (size_t)3 * a.nblocks));
+        chk(alloc(&a.ctr, 1));
+        chk(alloc(&a.io_pos, (size_t)3 * n)); chk(alloc(&a.io_vel, (size_t)3 * n));
+        if (r) return r;
+        r = alloc_nbr(a.cap);
+        if (r) return r;
+        MD_CUDA(cudaMemsetAsync(a.count, 0, sizeof(int) * a.ncells, stream));
+        MD_CUDA(cudaMemsetAsync(a.ctr, 0, sizeof(Counters), stream));
+        MD_CUDA(cudaMemsetAsync(a.nn, 0, sizeof(int) * n, stream));
+        MD_CUDA(cudaStreamSynchronize(stream));
+        return MD_OK;
+    }
+
+    int alloc_nbr(int cap) {
+        if (nbr_alloc) {
+            cudaFree(nbr_alloc);
+            nbr_alloc = nullptr;
+        }
+        size_t cols = (size_t)((a.n + 31) / 32) * 32;
+        size_t cnt = cols * (size_t)(cap > 0 ? cap : 1);
+        void* q = nullptr;
+        MD_CUDA(cudaMalloc(&q, cnt * sizeof(int)));
+        nbr_alloc = (int*)q;
+        a.nbr = nbr_alloc;
+        a.cap = cap;
+        plan.nbr_capacity = cap;
+        return MD_OK;
+    }
+
+    // ---- launches ------------------------------------------------------
+
+    template <class... T>
+    cudaError_t launch(void* f, unsigned grid, unsigned block, T&... args) {
+        void* p[] = {(void*)&args...};
+        launches++;
+        return cudaLaunchKernel(f, dim3(grid), dim3(block), p, 0, stream);
+    }
+
+    unsigned grid_atoms() const { return (unsigned)a.nblocks; }
+    unsigned grid_cells() const { return (unsigned)((a.ncells + kBlock - 1) / kBlock); }
+    unsigned grid_scatter() const {
+        int64_t m = a.n > a.ncells ? a.n : a.ncells;
+        return (unsigned)((m + kBlock - 1) / kBlock);
+    }
+
+    void* step_fn() const { return prm.cell_list_only ? kt.step_cells : kt.step_list; }
+
+    // The rebuild branch, as stream launches with the device-flag guard.
+    int rebuild_eager() {
+        int g = 1;
+        MD_CUDA(launch(kt.bin, grid_atoms(), kBlock, a, g));
+        MD_CUDA(launch(kt.scan_tiles, (unsigned)a.ntiles, kBlock, a, g));
+        MD_CUDA(launch(kt.scan_top, 1, 1024, a, g));
+        MD_CUDA(launch(kt.scan_apply, (unsigned)a.ntiles, kBlock, a, g));
+        MD_CUDA(launch(kt.scatter, grid_scatter(), kBlock, a, g));
+        MD_CUDA(launch(kt.cellsort, grid_cells(), kBlock, a, g));
+        MD_CUDA(launch(kt.gather, grid_atoms(), kBlock, a, g));
+        MD_CUDA(launch(kt.commit, grid_atoms(), kBlock, a, g));
+        if (!prm.cell_list_only) MD_CUDA(launch(kt.build, grid_atoms(), kBlock, a, g));
+        MD_CUDA(launch(kt.rebuild_done, 1, 32, a, g));
+        return MD_OK;
+    }
+
+    int step_kernel_eager(int mode) {
+        cudaGraphConditionalHandle none = 0;
+        int has = 0;
+        MD_CUDA(launch(step_fn(), grid_atoms(), kBlock, a, mode, none, has));
+        return MD_OK;
+    }
+
+    // ---- graphs ----------------------------------------------------------
+
+    void destroy_graphs() {
+        for (Chunk* c : {&big, &one}) {
+            if (c->e) cudaGraphExecDestroy(c->e);
+            if (c->g) cudaGraphDestroy(c->g);
+            c->e = nullptr;
+            c->g = nullptr;
+            c->K = 0;
+        }
+        graphs_ok = false;
+    }
+
+    template <class... T>
+    cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNode_t* out, void* f, unsigned grid,
+                           unsigned block, T&... args) {
+        void* p[] = {(void*)&args...};
+        NodeParams buf;
+        cudaGraphNodeParams& np = buf.get();
+        np.type = cudaGraphNodeTypeKernel;
+        np.kernel.func = f;
+        np.kernel.gridDim = dim3(grid);
+        np.kernel.blockDim = dim3(block);
+        np.kernel.sharedMemBytes = 0;
+        np.kernel.kernelParams = p;
+        return cudaGraphAddNode(out, g, dep, nullptr, dep ? 1 : 0, &np);
+    }
+
+    int build_body(cudaGraph_t body) {
+        int g = 0;
+        cudaGraphNode_t prev = nullptr, cur = nullptr;
+        auto chain = [&](cudaError_t e) -> cudaError_t {
+            prev = cur;
+            return e;
+        };
+        MD_CUDA(chain(add_kernel(body, nullptr, &cur, kt.bin, grid_atoms(), kBlock, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scan_tiles, (unsigned)a.ntiles, kBlock, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scan_top, 1, 1024, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scan_apply, (unsigned)a.ntiles, kBlock, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scatter, grid_scatter(), kBlock, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.cellsort, grid_cells(), kBlock, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.gather, grid_atoms(), kBlock, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.commit, grid_atoms(), kBlock, a, g)));
+        if (!prm.cell_list_only)
+            MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.build, grid_atoms(), kBlock, a, g)));
+        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.rebuild_done, 1, 32, a, g)));
+        return MD_OK;
+    }
+
+    int build_chunk(Chunk& c, int K) {
+        MD_CUDA(cudaGraphCreate(&c.g, 0));
+        std::vector<cudaGraphConditionalHandle> h(K);
+        for (int s = 0; s < K; s++) MD_CUDA(cudaGraphConditionalHandleCreate(&h[s], c.g, 0, 0));
+        cudaGraphNode_t prev = nullptr, node = nullptr;
+        MD_CUDA(add_kernel(c.g, nullptr, &node, kt.cond, 1, 32, a, h[0]));
+        prev = node;
+        int mode = kModeAuto;
+        for (int s = 0; s < K; s++) {
+            NodeParams buf;
+            cudaGraphNodeParams& cp = buf.get();
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h[s];
+            cp.conditional.type = cudaGraphCondTypeIf;
+            cp.conditional.size = 1;
+            cudaGraphNode_t ifn = nullptr;
+            MD_CUDA(cudaGraphAddNode(&ifn, c.g, &prev, nullptr, 1, &cp));
+            int r = build_body(cp.conditional.phGraph_out[0]);
+            if (r) return r;
+            cudaGraphConditionalHandle nxt = (s + 1 < K) ? h[s + 1] : 0;
+            int has = (s + 1 < K) ? 1 : 0;
+            MD_CUDA(add_kernel(c.g, &ifn, &node, step_fn(), grid_atoms(), kBlock, a, mode, nxt, has));
+            prev = node;
+        }
+        MD_CUDA(cudaGraphInstantiate(&c.e, c.g, 0));
+        c.K = K;
+        return MD_OK;
+    }
+
+    int ensure_graphs() {
+        if (graphs_ok) return MD_OK;
+        destroy_graphs();
+        int r = build_chunk(big, kChunk);
+        if (!r) r = build_chunk(one, 1);
+        if (r) {
+            destroy_graphs();
+            return r;
+        }
+        graphs_ok = true;
+        return MD_OK;
+    }
+
+    int graph_kernels_per_step() const { return 1; }
+
+    // Enqueues nsteps (rebuild?, force + integrate) pairs.
+    int run_steps(int64_t nsteps) {
+        if (nsteps <= 0) return MD_OK;
+        if (prm.use_graphs && !profiling) {
+            int r = ensure_graphs();
+            if (r) return r;
+            int64_t nb = nsteps / kChunk, rem = nsteps % kChunk;
+            for (int64_t b = 0; b < nb; b++) {
+                MD_CUDA(cudaGraphLaunch(big.e, stream));
+                graph_launches++;
+                launches += 1 + kChunk;
+            }
+            for (int64_t b = 0; b < rem; b++) {
+                MD_CUDA(cudaGraphLaunch(one.e, stream));
+                graph_launches++;
+                launches += 2;
+            }
+        } else {
+            if (profiling && (int64_t)ev.size() < 2 * nsteps) {
+                while ((int64_t)ev.size() < 2 * nsteps) {
+                    cudaEvent_t e;
+                    MD_CUDA(cudaEventCreate(&e));
+                    ev.push_back(e);
+                }
+            }
+            for (int64_t s = 0; s < nsteps; s++) {
+                int r = rebuild_eager();
+                if (r) return r;
+                if (profiling) MD_CUDA(cudaEventRecord(ev[2 * s], stream));
+                r = step_kernel_eager(kModeAuto);
+                if (r) return r;
+                if (profiling) MD_CUDA(cudaEventRecord(ev[2 * s + 1], stream));
+            }
+            if (profiling) {
+                MD_CUDA(cudaStreamSynchronize(stream));
+                for (int64_t s = 0; s < nsteps; s++) {
+                    float ms = 0.f;
+                    MD_CUDA(cudaEventElapsedTime(&ms, ev[2 * s], ev[2 * s + 1]));
+                    step_ms += ms;
+                }
+                step_launches += nsteps;
+            }
+        }
+        steps_run += nsteps;
+        return MD_OK;
+    }
+
+    int read_counters(Counters* c) {
+        MD_CUDA(cudaMemcpyAsync(c, a.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, stream));
+        MD_CUDA(cudaStreamSynchronize(stream));
+        return MD_OK;
+    }
+
+    int check_fatal(const Counters& c) {
+        if (c.error & (kErrUnstable | kErrClose)) {
+            err = (c.error & kErrClose) ? "two atoms came closer than the fixed-point force range allows"
+                                        : "non-finite coordinate or an atom moved more than one cell between rebuilds";
+            return MD_EUNSTABLE;
+        }
+        return MD_OK;
+    }
+
+    // Enlarges the neighbour capacity after an overflow and rebuilds.
+    int regrow(const Counters& c) {
+        int need = c.need_cap > a.cap ? c.need_cap : a.cap + 4;
+        int cap = (int)std::ceil(need * 1.25) + 4;
+        cap = (cap + 3) & ~3;
+        if (cap > 8192) {
+            err = "neighbour capacity would exceed 8192 entries per atom";
+            return MD_EOVERFLOW;
+        }
+        MD_CUDA(cudaStreamSynchronize(stream));
+        destroy_graphs();
+        int r = alloc_nbr(cap);
+        if (r) return r;
+        MD_CUDA(launch(kt.clear_overflow, 1, 32, a.ctr));
+        return rebuild_eager();
+    }
+
+    int finish_pending(int64_t* steps_left_out) {
+        for (int attempt = 0; attempt < 16; attempt++) {
+            Counters c;
+            int r = read_counters(&c);
+            if (r) return r;
+            r = check_fatal(c);
+            if (r) return r;
+            if (c.error & kErrOverflow) {
+                r = regrow(c);
+                if (r) return r;
+                // the step that met the overflow has not run yet
+                Counters c2;
+                r = read_counters(&c2);
+                if (r) return r;
+                if (c2.error & kErrOverflow) continue;
+                r = run_steps(c2.steps_left);
+                if (r) return r;
+                continue;
+            }
+            if (steps_left_out) *steps_left_out = c.steps_left;
+            return MD_OK;
+        }
+        err = "neighbour list kept overflowing";
+        return MD_EOVERFLOW;
+    }
+
+    // ---- API -------------------------------------------------------------
+
+    int set_state(const double* pos, const double* vel, bool device) override {
+        DevGuard dg(this->device);
+        if (!pos || !vel) {
+            err = "NULL state array";
+            return MD_EINVAL;
+        }
+        size_t bytes = sizeof(double) * 3 * (size_t)a.n;
+        cudaMemcpyKind k = device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        MD_CUDA(cudaMemcpyAsync(a.io_pos, pos, bytes, k, stream));
+        MD_CUDA(cudaMemcpyAsync(a.io_vel, vel, bytes, k, stream));
+        MD_CUDA(launch(kt.reset_counters, 1, 32, a.ctr));
+        MD_CUDA(launch(kt.set_state, grid_atoms(), kBlock, a));
+        int r = rebuild_eager();
+        if (r) return r;
+        for (int attempt = 0; attempt < 8; attempt++) {
+            Counters c;
+            r = read_counters(&c);
+            if (r) return r;
+            r = check_fatal(c);
+            if (r) return r;
+            if (!(c.error & kErrOverflow)) break;
+            r = regrow(c);
+            if (r) return r;
+        }
+        r = step_kernel_eager(kModeInit);
+        if (r) return r;
+        Counters c;
+        r = read_counters(&c);
+        if (r) return r;
+        r = check_fatal(c);
+        if (r) return r;
+        have_state = true;
+        return MD_OK;
+    }
+
+    int step(int64_t n) override {
+        DevGuard dg(device);
+        if (n <= 0) return MD_OK;
+        if (!have_state) {
+            err = "md_step before md_set_state";
+            return MD_ESTATE;
+        }
+        long long nn = (long long)n;
+        MD_CUDA(launch(kt.kickdrift, grid_atoms(), kBlock, a, nn));
+        int r = run_steps(n);
+        if (r) return r;
+        int64_t left = 0;
+        r = finish_pending(&left);
+        if (r) return r;
+        if (left != 0) {
+            err = "step counter did not reach zero";
+            return MD_ECUDA;
+        }
+        return MD_OK;
+    }
+
+    int measure(md_measure_t* out) override {
+        DevGuard dg(device);
+        if (!out) {
+            err = "NULL output";
+            return MD_EINVAL;
+        }
+        if (!have_state) {
+            err = "md_measure before md_set_state";
+            return MD_ESTATE;
+        }
+        MD_CUDA(launch(kt.finalize, 1, kBlock, a));
+        Counters c;
+        int r = read_counters(&c);
+        if (r) return r;
+        std::memset(out, 0, sizeof(*out));
+        double V = box[0] * box[1] * box[2];
+        out->ke = c.ke;
+        out->pe = c.pe;
+        out->virial = c.virial;
+        out->volume = V;
+        out->pressure = (2.0 * c.ke + c.virial) / (3.0 * V);
+        out->temperature = 2.0 * c.ke / (3.0 * (double)a.n);
+        out->e_tot_per_atom = (c.ke + c.pe) / (double)a.n;
+        out->step = c.step;
+        out->rebuilds = c.rebuilds;
+        out->reorders = c.reorders;
+        out->list_entries = c.list_entries;
+        out->max_neighbors = c.max_nn;
+        out->max_occupancy = c.max_occ;
+        out->nbr_capacity = a.cap;
+        return MD_OK;
+    }
+
+    int get_state(double* pos, double* vel, bool device) override {
+        DevGuard dg(this->device);
+        if (!pos || !vel) {
+            err = "NULL output";
+            return MD_EINVAL;
+        }
+        if (!have_state) {
+            err = "md_get_state before md_set_state";
+            return MD_ESTATE;
+        }
+        MD_CUDA(launch(kt.get_state, grid_atoms(), kBlock, a));
+        size_t bytes = sizeof(double) * 3 * (size_t)a.n;
+        cudaMemcpyKind k = device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        MD_CUDA(cudaMemcpyAsync(pos, a.io_pos, bytes, k, stream));
+        MD_CUDA(cudaMemcpyAsync(vel, a.io_vel, bytes, k, stream));
+        MD_CUDA(cudaStreamSynchronize(stream));
+        return MD_OK;
+    }
+
+    int get_forces(double* f) override {
+        DevGuard dg(device);
+        if (!f) {
+            err = "NULL output";
+            return MD_EINVAL;
+        }
+        if (!have_state) {
+            err = "md_get_forces before md_set_state";
+            return MD_ESTATE;
+        }
+        double* tmp = a.io_pos;
+        MD_CUDA(launch(kt.get_forces, grid_atoms(), kBlock, a, tmp));
+        MD_CUDA(cudaMemcpyAsync(f, tmp, sizeof(double) * 3 * (size_t)a.n, cudaMemcpyDeviceToHost, stream));
+        MD_CUDA(cudaStreamSynchronize(stream));
+        return MD_OK;
+    }
+
+    int debug_cells(int32_t* cell) override {
+        DevGuard dg(device);
+        if (!cell) {
+            err = "NULL output";
+            return MD_EINVAL;
+        }
+        if (!have_state) {
+            err = "md_debug_cells before md_set_state";
+            return MD_ESTATE;
+        }
+        int* tmp = a.rank;
+        MD_CUDA(launch(kt.get_cells, grid_atoms(), kBlock, a, tmp));
+        MD_CUDA(cudaMemcpyAsync(cell, tmp, sizeof(int) * (size_t)a.n, cudaMemcpyDeviceToHost, stream));
+        MD_CUDA(cudaStreamSynchronize(stream));
+        return MD_OK;
+    }
+
+    int debug_neighbors(int64_t* count, int64_t* entries, int32_t* pairs, int64_t cap) override {
+        DevGuard dg(device);
+        if (!count) {
+            err = "NULL count";
+            return MD_EINVAL;
+        }
+        if (!have_state) {
+            err = "md_debug_neighbors before md_set_state";
+            return MD_ESTATE;
+        }
+        if (prm.cell_list_only) {
+            err = "no neighbour list in cell-list-only mode";
+            return MD_ESTATE;
+        }
+        int64_t n = a.n;
+        size_t cols = (size_t)((n + 31) / 32) * 32;
+        std::vector<int> nn(n), perm(n), nbr(cols * (size_t)a.cap);
+        MD_CUDA(cudaMemcpyAsync(nn.data(), a.nn, sizeof(int) * n, cudaMemcpyDeviceToHost, stream));
+        MD_CUDA(cudaMemcpyAsync(perm.data(), a.perm, sizeof(int) * n, cudaMemcpyDeviceToHost, stream));
+        MD_CUDA(cudaMemcpyAsync(nbr.data(), a.nbr, sizeof(int) * nbr.size(), cudaMemcpyDeviceToHost, stream));
+        MD_CUDA(cudaStreamSynchronize(stream));
+        int64_t np = 0, ne = 0;
+        for (int64_t i = 0; i < n; i++) {
+            const int* col = nbr.data() + ((size_t)(i >> 5) * a.cap) * 32 + (i & 31);
+            for (int m = 0; m < nn[i]; m++) {
+                int j = col[(size_t)m * 32] & kIndexMask;
+                if (j >= n) {
+                    err = "neighbour entry out of range";
+                    return MD_ECUDA;
+                }
+                ne++;
+                int ui = perm[i], uj = perm[j];
+                if (ui < uj) {
+                    if (pairs && np < cap) {
+                        pairs[2 * np + 0] = ui;
+                        pairs[2 * np + 1] = uj;
+                    }
+                    np++;
+                }
+            }
+        }
+        *count = np;
+        if (entries) *entries = ne;
+        return MD_OK;
+    }
+
+    int get_plan(md_plan_t* out) override {
+        if (!out) return MD_EINVAL;
+        *out = plan;
+        out->nbr_capacity = a.cap;
+        return MD_OK;
+    }
+
+    int set_profiling(int on) override {
+        profiling = on != 0;
+        return MD_OK;
+    }
+
+    int kernel_stats(md_kernel_stats_t* out) override {
+        DevGuard dg(device);
+        if (!out) return MD_EINVAL;
+        Counters c;
+        int r = read_counters(&c);
+        if (r) return r;
+        std::memset(out, 0, sizeof(*out));
+        // every rebuild branch that ran launched its kernels
+        int per_rebuild = prm.cell_list_only ? 9 : 10;
+        int64_t body = prm.use_graphs && !profiling ? (int64_t)c.rebuilds * per_rebuild : 0;
+        out->launches = launches + body;
+        out->step_kernel_launches = step_launches;
+        out->step_kernel_ms = step_ms;
+        out->step_kernel_atoms = step_launches * a.n;
+        int64_t base = P::kFp64 ? 188 : 120;
+        out->step_kernel_bytes = step_launches * (base * a.n + 4 * c.list_entries);
+        return MD_OK;
+    }
+
+    int sync() override {
+        DevGuard dg(device);
+        MD_CUDA(cudaStreamSynchronize(stream));
+        Counters c;
+        int r = read_counters(&c);
+        if (r) return r;
+        return check_fatal(c);
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+struct md_handle {
+    SimBase* sim;
+};
+
+extern "C" {
+
+void md_default_params(md_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->precision = MD_PREC_MIXED;
+    p->reorder_interval = 100;
+    p->cell_list_only = 0;
+    p->even_cells = 0;
+    p->nbr_capacity = 0;
+    p->use_graphs = 1;
+    p->device = -1;
+    p->ushift = NAN;
+    p->stream = nullptr;
+}
+
+int md_plan(const double box[3], int64_t n, double rc, double skin, double dt, const md_params* p,
+            md_plan_t* out) {
+    std::string why;
+    int r = resolve_plan(box, n, rc, skin, dt, p, out, &why);
+    if (r) g_create_error = why;
+    return r;
+}
+
+int md_create(const double box[3], int64_t n, double rc, double skin, double dt, const md_params* p,
+              md_handle** out) {
+    if (!out) {
+        g_create_error = "NULL output handle";
+        return MD_EINVAL;
+    }
+    *out = nullptr;
+    md_params d;
+    md_default_params(&d);
+    const md_params* q = p ? p : &d;
+    SimBase* s = nullptr;
+    int r;
+    if (q->precision == MD_PREC_FP64) {
+        auto* sim = new Sim<F64>();
+        r = sim->create(box, n, rc, skin, dt, q);
+        s = sim;
+    } else {
+        auto* sim = new Sim<Mixed>();
+        r = sim->create(box, n, rc, skin, dt, q);
+        s = sim;
+    }
+    if (r) {
+        g_create_error = s->err;
+        delete s;
+        return r;
+    }
+    *out = new md_handle{s};
+    return MD_OK;
+}
+
+#define MD_H(h) \
+    if (!(h) || !(h)->sim) return MD_EINVAL
+
+int md_set_state(md_handle* h, const double* pos, const double* vel) {
+    MD_H(h);
+    return h->sim->set_state(pos, vel, false);
+}
+int md_set_state_device(md_handle* h, const double* pos, const double* vel) {
+    MD_H(h);
+    return h->sim->set_state(pos, vel, true);
+}
+int md_step(md_handle* h, int64_t nsteps) {
+    MD_H(h);
+    return h->sim->step(nsteps);
+}
+int md_measure(md_handle* h, md_measure_t* out) {
+    MD_H(h);
+    return h->sim->measure(out);
+}
+int md_get_state(md_handle* h, double* pos, double* vel) {
+    MD_H(h);
+    return h->sim->get_state(pos, vel, false);
+}
+int md_get_state_device(md_handle* h, double* pos, double* vel) {
+    MD_H(h);
+    return h->sim->get_state(pos, vel, true);
+}
+int md_get_forces(md_handle* h, double* f) {
+    MD_H(h);
+    return h->sim->get_forces(f);
+}
+int md_debug_cells(md_handle* h, int32_t* cell) {
+    MD_H(h);
+    return h->sim->debug_cells(cell);
+}
+int md_debug_neighbors(md_handle* h, int64_t* count, int64_t* entries, int32_t* pairs, int64_t capacity) {
+    MD_H(h);
+    return h->sim->debug_neighbors(count, entries, pairs, capacity);
+}
+int md_get_plan(md_handle* h, md_plan_t* out) {
+    MD_H(h);
+    return h->sim->get_plan(out);
+}
+int md_set_profiling(md_handle* h, int on) {
+    MD_H(h);
+    return h->sim->set_profiling(on);
+}
+int md_kernel_stats(md_handle* h, md_kernel_stats_t* out) {
+    MD_H(h);
+    return h->sim->kernel_stats(out);
+}
+int md_sync(md_handle* h) {
+    MD_H(h);
+    return h->sim->sync();
+}
+void md_destroy(md_handle* h) {
+    if (!h) return;
+    delete h->sim;
+    delete h;
+}
+const char* md_last_error(const md_handle* h) {
+    if (!h || !h->sim) return g_create_error.c_str();
+    return h->sim->err.c_str();
+}
+const char* md_strerror(int code) {
+    switch (code) {
+        case MD_OK: return "ok";
+        case MD_EINVAL: return "invalid argument";
+        case MD_ENOMEM: return "out of memory";
+        case MD_ECUDA: return "CUDA error";
+        case MD_ESTATE: return "invalid call order";
+        case MD_EOVERFLOW: return "neighbour list overflow";
+        case MD_EUNSTABLE: return "unstable simulation";
+        case MD_ENODEV: return "no CUDA device";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// md_common.cuh -- device-state layout shared by the kernels and the host
+// runtime of libmd.  Internal; the public interface is include/md.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace md {
+
+// Threads per block for every per-atom / per-slot kernel.
+constexpr int kBlock = 256;
+// Elements per block of the cell-count scan (kBlock threads x 8).
+constexpr int kScanTile = 2048;
+// Neighbour entries are j | code << kCodeShift; code packs the cell offset
+// (d_x+1) | (d_y+1) << 2 | (d_z+1) << 4 of j's cell relative to i's cell, the
+// periodic-image information beta of Sec. 2.2 in 6 high bits.
+constexpr int kCodeShift = 26;
+constexpr int kIndexMask = (1 << kCodeShift) - 1;
+constexpr int64_t kMaxAtoms = int64_t(1) << kCodeShift;
+// Fixed-point scale of the mixed form's per-atom sums.
+constexpr double kFixScale = 4294967296.0;       // 2^32
+constexpr float kFixScaleF = 4294967296.0f;
+constexpr float kFixInvF = 2.3283064365386963e-10f;  // 2^-32
+constexpr double kFixInv = 2.3283064365386963e-10;
+
+// Error bits recorded on the device.
+enum : int {
+    kErrOverflow = 1,   // neighbour list longer than its capacity
+    kErrUnstable = 2,   // atom left its cell neighbourhood / non-finite value
+    kErrClose = 4,      // pair closer than the fixed-point range allows
+};
+
+// Step-kernel modes.
+enum : int {
+    kModeInit = 0,  // forces of the loaded state; velocities untouched
+    kModeAuto = 1,  // a full step, or the final half-kick when one step is left
+};
+
+// Counters and flags kept on the device (one per handle).
+struct Counters {
+    int error;                 // kErr* bits
+    int need_cap;              // largest neighbour count seen by an overflowing build
+    int rebuild_flag;          // the next rebuild branch must run
+    int reorder_now;           // the pending rebuild also reorders the atoms
+    int parity;                // which pair-coordinate buffer is current (0 = A)
+    int max_nn;                // largest neighbour count at the last build
+    int max_occ;               // largest cell occupancy at the last binning
+    unsigned int ticket;       // last-block-done counter (reset by the last block)
+    unsigned int far_flag;     // some atom moved skin/2 since the last build
+    int close_flag;            // a pair came too close during the running step
+    long long steps_left;      // steps still to run in the current md_step
+    long long step;            // steps completed since the state was loaded
+    long long since_reorder;   // steps since the last reorder
+    long long rebuilds;        // rebuilds since the state was loaded
+    long long reorders;        // reorders since the state was loaded
+    long long list_entries;    // neighbour-list length at the last build
+    // reduced measurement of the last finalize
+    double ke, pe, virial;
+};
+
+// Precision forms.  real: pair arithmetic, build offsets and saved forces;
+// vel: velocity storage; pos4: gathered coordinates (x, y, z, payload).
+struct Mixed {
+    using real = float;
+    using vel = float;
+    using pos4 = float4;
+    static constexpr bool kFp64 = false;
+};
+struct F64 {
+    using real = double;
+    using vel = double;
+    using pos4 = double4_32a;
+    static constexpr bool kFp64 = true;
+};
+
+// Everything the kernels need, passed by value.  Device pointers only.
+template <class P>
+struct Args {
+    using real = typename P::real;
+    using vel = typename P::vel;
+    using pos4 = typename P::pos4;
+
+    int64_t n;          // atoms
+    int cap;            // neighbour slots per atom
+    int ncells;
+    int G[3];
+    int ntiles;         // scan tiles
+    int nblocks;        // ceil(n / kBlock)
+    int cell_list_only;
+    int reorder_interval;
+
+    double L[3], hL[3], invL[3], invW[3];
+    double w[3];        // cell widths
+    double hw[3];       // half cell widths
+    float wf[3];
+    double dt, h;       // time step and half step
+    float dtf, hf;
+    double rc2;         // r_c^2
+    float rc2f;
+    double rn2;         // r_n^2
+    float rn2_lo, rn2_hi;  // FP32 pre-filter band around r_n^2
+    double ushift;
+    float ushiftf;
+    double thr2;        // (skin/2)^2
+    float thr2f;
+    float close2f;      // pairs closer than this flag kErrClose
+    double close2;
+
+    // per-atom state, storage order
+    int* cell;          // cell index of the last binning
+    int* perm;          // storage index -> user id
+    int* rank;          // arrival rank within the cell (binning scratch)
+    real* pbx; real* pby; real* pbz;   // cell-relative offset at the last build
+    double* ox; double* oy; double* oz; // displacement since the last build
+    vel* vx; vel* vy; vel* vz;
+    real* fx; real* fy; real* fz;      // forces of the last completed step
+    pos4* pA; pos4* pB;                // current cell-relative coordinates (ping-pong)
+    pos4* cand;                        // coordinates in cell order + storage index
+
+    // reorder scratch (same shapes as the state)
+    int* s_cell; int* s_perm;
+    real* s_pbx; real* s_pby; real* s_pbz;
+    double* s_ox; double* s_oy; double* s_oz;
+    vel* s_vx; vel* s_vy; vel* s_vz;
+
+    // cells
+    int* count;         // [ncells] atoms per cell (kept zero between binnings)
+    int* cell_start;    // [ncells + 1]
+    int* order;         // [n] storage index of each cell-ordered slot
+    int* tile_sum;      // [ntiles] then exclusive tile offsets
+
+    // neighbour list: entry m of atom i at ((i / 32) * cap + m) * 32 + i % 32
+    int* nbr;
+    int* nn;            // [n] entries per atom
+
+    double* part;       // [3 * nblocks] per-block KE, PE, W
+    Counters* ctr;
+
+    double* io_pos;     // [3 n] staging for set/get (user order, AoS)
+    double* io_vel;     // [3 n]
+};
+
+}  // namespace md

@@ -1,0 +1,36 @@
+// md_table.h -- addresses of the kernels of one precision form, handed from
+// the kernel translation units to the host runtime (graph nodes and stream
+// launches take kernels by address).
+#pragma once
+
+namespace md {
+
+template <class P>
+struct KernelTable {
+    void* set_state;
+    void* bin;
+    void* scan_tiles;
+    void* scan_top;
+    void* scan_apply;
+    void* scatter;
+    void* cellsort;
+    void* gather;
+    void* commit;
+    void* build;
+    void* rebuild_done;
+    void* cond;
+    void* kickdrift;
+    void* step_list;
+    void* step_cells;
+    void* finalize;
+    void* get_state;
+    void* get_forces;
+    void* get_cells;
+    void* reset_counters;
+    void* clear_overflow;
+};
+
+template <class P>
+KernelTable<P> make_kernel_table();
+
+}  // namespace md

@@ -1,0 +1,142 @@
+"""Determinism, reordering, capacity growth, error reporting and energy
+conservation of the CUDA path (through the C ABI)."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_0911_5631_gb300 as md
+from mdcheck import DT, RC, ensure_built, sim, state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _run(prec, steps=300, n=4000, seed=7, **kw):
+    pos, vel, L = state(n, 0.8, 1.5, seed, jitter=0.15)
+    s = sim(pos, vel, L, skin=0.4, precision=prec, **kw)
+    s.step(steps)
+    p, v = s.get_state()
+    f = s.forces()
+    m = s.measure()
+    s.close()
+    return p, v, f, m
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_run_twice_bitwise(prec):
+    a = _run(prec)
+    b = _run(prec)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+    assert a[3]["ke"] == b[3]["ke"] and a[3]["pe"] == b[3]["pe"]
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_graphs_and_stream_launches_agree_bitwise(prec):
+    a = _run(prec, use_graphs=True)
+    b = _run(prec, use_graphs=False)
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_mixed_trajectory_independent_of_reordering():
+    # int64 force sums make every atom's result independent of storage order
+    ref = _run("mixed", reorder_interval=0)
+    assert ref[3]["reorders"] == 1  # the initial sort at load
+    for interval in (1, 7, 100):
+        got = _run("mixed", reorder_interval=interval)
+        assert got[3]["reorders"] > 1 or interval == 100
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+        assert np.array_equal(got[2], ref[2])
+
+
+def test_fp64_reordering_changes_only_rounding():
+    ref = _run("fp64", reorder_interval=0, steps=100)
+    got = _run("fp64", reorder_interval=1, steps=100)
+    assert np.abs(got[1] - ref[1]).max() < 1e-11
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_capacity_growth_is_transparent(prec):
+    a = _run(prec, nbr_capacity=4, steps=200)
+    b = _run(prec, steps=200)
+    assert a[3]["nbr_capacity"] > 4
+    for x, y in zip(a[:3], b[:3]):
+        assert np.array_equal(x, y)
+
+
+def test_step_chunking_is_transparent():
+    pos, vel, L = state(2048, 0.8, 1.0, 3, jitter=0.1)
+    s1 = sim(pos, vel, L)
+    s1.step(100)
+    s2 = sim(pos, vel, L)
+    for k in (1, 31, 32, 33, 3):
+        s2.step(k)
+    p1, v1 = s1.get_state()
+    p2, v2 = s2.get_state()
+    # the last step of a call stores v_n and the next call's first kick
+    # repeats exactly the operation the fused kernel would have done
+    assert np.array_equal(p1, p2) and np.array_equal(v1, v2)
+    assert s1.measure()["step"] == s2.measure()["step"] == 100
+    s1.close()
+    s2.close()
+
+
+def test_errors_are_reported():
+    pos, vel, L = state(256, 0.8, 1.0, 1)
+    s = md.Simulation(L, 256, RC, 0.4, DT)
+    with pytest.raises(md.MDError) as e:
+        s.step(5)
+    assert e.value.code == md.MD_ESTATE
+    s.step(0)  # no-op
+    with pytest.raises(md.MDError) as e:
+        s.set_state(np.full((256, 3), np.nan), vel)
+    assert e.value.code == md.MD_EUNSTABLE
+    s.close()
+    # two atoms far inside the core: reported, not silently wrapped
+    L = np.array([6.0, 6.0, 6.0])
+    pos = np.array([[0.0, 0.0, 0.0], [0.2, 0.0, 0.0]])
+    s = md.Simulation(L, 2, RC, 0.4, DT)
+    with pytest.raises(md.MDError) as e:
+        s.set_state(pos, np.zeros((2, 3)))
+    assert e.value.code == md.MD_EUNSTABLE
+    s.close()
+
+
+def test_state_round_trip_and_device_pointers():
+    torch = pytest.importorskip("torch")
+    pos, vel, L = state(1372, 0.8, 1.0, 9, jitter=0.1)
+    s = sim(pos, vel, L)
+    p, v = s.get_state()
+    pw = oracle.wrap(pos, L)
+    assert np.abs(p - pw).max() < 1e-13
+    assert np.abs(v - vel).max() < 1e-7  # FP32 velocity storage
+    tp = torch.tensor(pos, device="cuda")
+    tv = torch.tensor(vel, device="cuda")
+    s.set_state(tp, tv)
+    op = torch.empty_like(tp)
+    ov = torch.empty_like(tv)
+    s.get_state(op, ov)
+    assert np.abs(op.cpu().numpy() - p).max() == 0.0
+    s.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_energy_drift(prec):
+    # soft-sphere fluid at rho 0.8, T 1, skin 0.4: |<e_tot> over the last
+    # 1000 steps - <e_tot> over steps 1000-2000| per atom after 10^4 steps
+    n = 32000
+    pos, vel, L = state(n, 0.8, 1.0, 2)
+    s = sim(pos, vel, L, precision=prec)
+    e = []
+    for k in range(1000):
+        s.step(10)
+        e.append(s.measure()["e_tot_per_atom"])
+    e = np.array(e)
+    drift = abs(e[-100:].mean() - e[100:200].mean())
+    assert drift <= 1e-4
+    s.close()

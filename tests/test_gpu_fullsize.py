@@ -1,0 +1,70 @@
+"""Parity at the full benchmark sizes, in the launch configuration the
+benchmark times (graphs, reorder every 100 steps): spot checks the oracle
+can compute atom by atom, plus properties that hold at any size."""
+import numpy as np
+import pytest
+
+import oracle
+from mdcheck import DT, FORCE_TOL, RC, ensure_built, rel_rms, sim, state
+from paper_0911_5631_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _sampled_force_check(s, L, prec, nsample=64, seed=0):
+    p, v = s.get_state()
+    f = s.forces()
+    n = p.shape[0]
+    idx = np.random.default_rng(seed).choice(n, nsample, replace=False)
+    fr, ur = oracle.forces_sampled(p, L, RC, 1.0, idx)
+    assert rel_rms(f[idx], fr) <= FORCE_TOL[prec]
+    scale = float(np.sqrt(np.mean(fr ** 2)))
+    err = np.linalg.norm(f[idx] - fr, axis=1)
+    assert np.all(err <= 20 * FORCE_TOL[prec] * (np.linalg.norm(fr, axis=1) + scale))
+    return p, v, f
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_one_million_atoms(prec):
+    # 1,048,576 atoms: FCC 64^3 x 4, rho 0.8, T 1, skin 0.4, reorder every 100
+    cfg = inputs.WORKLOADS["wca_fcc64_n1m"]
+    pos, vel, L = state(cfg["n"], cfg["rho"], cfg["T"], cfg["seed"])
+    s = sim(pos, vel, L, skin=cfg["skin"], precision=prec, reorder_interval=100)
+    s.step(300)
+    m = s.measure()
+    assert m["step"] == 300 and m["rebuilds"] > 5 and m["reorders"] >= 3
+    p, v, f = _sampled_force_check(s, L, prec)
+    # momentum: zero at start, conserved up to rounding
+    assert np.abs(v.sum(axis=0)).max() < (1e-2 if prec == "mixed" else 1e-8)
+    # exact neighbour sets of sampled atoms after a fresh build here
+    s.set_state(p, v)
+    pairs, entries = s.neighbor_pairs()
+    rn = RC + cfg["skin"]
+    for i in np.random.default_rng(1).choice(cfg["n"], 12, replace=False):
+        mine = np.sort(np.concatenate([pairs[pairs[:, 0] == i, 1], pairs[pairs[:, 1] == i, 0]]))
+        ref = oracle.neighbors_of(p, L, rn, i)
+        diff = set(mine.tolist()) ^ set(ref.tolist())
+        for j in diff:
+            assert abs(oracle.pair_r2(p, L, i, j) - rn * rn) < 1e-10
+    assert entries == 2 * len(pairs)
+    assert 11.0 < entries / cfg["n"] < 13.0  # N_p / N_a near 12 for this state
+    s.close()
+
+
+@pytest.mark.parametrize("rho,T", [(1.0, 2.0), (0.6, 0.7)])
+def test_eight_million_atoms(rho, T):
+    # 8,388,608 atoms: FCC 128^3 x 4, mixed form; at rho 1.0 every
+    # nearest-neighbour pair of the start lattice sits exactly on r_c
+    n = 8388608
+    pos, vel, L = state(n, rho, T, 3)
+    s = sim(pos, vel, L, skin=0.4, precision="mixed")
+    s.step(60)
+    m = s.measure()
+    assert m["step"] == 60
+    _sampled_force_check(s, L, "mixed", nsample=24)
+    s.close()

@@ -1,0 +1,183 @@
+"""Parity of the CUDA path with the FP64 oracle on seeded inputs, through the
+C ABI: cell assignment and neighbour-pair sets (exact), forces, energies and
+virial (within the stated tolerances), and short trajectory segments."""
+import numpy as np
+import pytest
+
+import oracle
+from mdcheck import (DT, FORCE_TOL, RC, assert_same_pairs, ensure_built, min_image, oracle_grid,
+                     rel_rms, sim, state)
+
+pytestmark = pytest.mark.gpu
+
+# (n, rho, T, skin, lattice jitter, box aspect, seed): several 256-atom tiles,
+# ragged counts, dense/hot and dilute/cold states, a non-cubic box, and a
+# 3-cell grid.
+CASES = [
+    (2048, 0.8, 1.0, 0.4, 0.15, (1, 1, 1), 1),
+    (1000, 0.8, 1.0, 0.4, 0.20, (1, 1, 1), 2),
+    (4000, 1.0, 2.0, 0.4, 0.08, (1, 1, 1), 3),
+    (3001, 0.6, 0.7, 0.3, 0.30, (1.0, 1.4, 0.8), 4),
+    (256, 0.8, 1.0, 0.6, 0.20, (1, 1, 1), 5),
+]
+IDS = ["n2048", "n1000", "n4000_dense", "n3001_rect", "n256_g3"]
+PRECS = ["mixed", "fp64"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def _setup(case, prec, **kw):
+    n, rho, T, skin, jit, aspect, seed = case
+    pos, vel, L = state(n, rho, T, seed, jitter=jit, aspect=aspect)
+    s = sim(pos, vel, L, skin=skin, precision=prec, **kw)
+    return s, pos, vel, L, skin
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_cells_bit_exact(case, prec):
+    s, pos, vel, L, skin = _setup(case, prec)
+    G = np.array(s.plan()["G"])
+    pw = oracle.wrap(pos, L)
+    assert np.array_equal(s.cells(), oracle.cell_of(pw, L, G))
+    m = s.measure()
+    counts = np.bincount(oracle.cell_of(pw, L, G), minlength=int(np.prod(G)))
+    assert m["max_occupancy"] == counts.max()
+    s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_neighbor_pairs_match_oracle(case, prec):
+    s, pos, vel, L, skin = _setup(case, prec)
+    pw = oracle.wrap(pos, L)
+    rn = RC + skin
+    pairs, entries = s.neighbor_pairs()
+    assert entries == 2 * len(pairs)  # full list: every pair in both columns
+    ref = oracle.pairs_cells(pw, L, oracle_grid(L, rn), rn)
+    assert_same_pairs(pairs, ref, pw, L, rn)
+    m = s.measure()
+    assert m["list_entries"] == entries
+    s.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_pair_sets_identical_across_precisions(case):
+    a = _setup(case, "mixed")[0]
+    b = _setup(case, "fp64")[0]
+    pa, pb = a.neighbor_pairs()[0], b.neighbor_pairs()[0]
+    assert np.array_equal(pa[np.lexsort(pa.T[::-1])], pb[np.lexsort(pb.T[::-1])])
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_forces_energy_virial(case, prec):
+    s, pos, vel, L, skin = _setup(case, prec)
+    pw = oracle.wrap(pos, L)
+    f_ref, U, W = oracle.forces_cells(pw, L, oracle_grid(L, RC), RC, 1.0)
+    f = s.forces()
+    assert np.abs(f_ref).max() > 10.0  # the jitter puts pairs inside r_c
+    assert rel_rms(f, f_ref) <= FORCE_TOL[prec]
+    m = s.measure()
+    tol = FORCE_TOL[prec]
+    assert m["pe"] == pytest.approx(U, rel=10 * tol)
+    assert m["virial"] == pytest.approx(W, rel=10 * tol)
+    ke_ref = 0.5 * np.sum(vel * vel)
+    # the mixed form stores velocities in FP32
+    assert m["ke"] == pytest.approx(ke_ref, rel=1e-14 if prec == "fp64" else 2e-7)
+    n = pos.shape[0]
+    V = float(np.prod(L))
+    assert m["pressure"] == pytest.approx((2 * m["ke"] + m["virial"]) / (3 * V), rel=1e-14)
+    assert m["temperature"] == pytest.approx(2 * m["ke"] / (3 * n), rel=1e-14)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_newton_third_law_in_result(prec):
+    s, pos, vel, L, skin = _setup(CASES[0], prec)
+    f = s.forces()
+    scale = np.abs(f).max()
+    # mixed: int64 pair terms cancel exactly; the FP32 conversion of each
+    # atom's sum leaves only rounding
+    tol = 1e-6 if prec == "mixed" else 1e-12
+    assert np.abs(f.sum(axis=0)).max() <= tol * scale * np.sqrt(pos.shape[0])
+    s.close()
+
+
+def _trajectory_tol(prec, f_rms, k):
+    # velocity error after k steps from the same state: k dt times the force
+    # error allowed per step, with a factor 10 for growth along the segment
+    fe = FORCE_TOL[prec] * f_rms
+    dv = 10.0 * k * DT * fe + (1e-7 if prec == "mixed" else 1e-14)
+    return dv, k * DT * dv + 1e-13
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", CASES[:4], ids=IDS[:4])
+def test_trajectory_segment(case, prec):
+    k = 40
+    s, pos, vel, L, skin = _setup(case, prec)
+    pw = oracle.wrap(pos, L)
+    ref = oracle.run(pw, vel, L, RC, skin, DT, k)
+    s.step(k)
+    p, v = s.get_state()
+    f_rms = float(np.sqrt(np.mean(ref["f"] ** 2)))
+    dv, dx = _trajectory_tol(prec, f_rms, k)
+    assert np.sqrt(np.mean((v - ref["vel"]) ** 2)) <= dv
+    assert np.sqrt(np.mean(min_image(p - ref["pos"], L) ** 2)) <= dx
+    assert np.all(p >= -np.asarray(L) / 2) and np.all(p < np.asarray(L) / 2)
+    m = s.measure()
+    assert m["step"] == k
+    assert m["rebuilds"] >= 1
+    e_gpu = m["ke"] + m["pe"]
+    e_ref = ref["ke"][-1] + ref["pe"][-1]
+    assert e_gpu == pytest.approx(e_ref, rel=1e-5 if prec == "mixed" else 1e-11)
+    s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_cell_list_only_segments(prec):
+    # soft-sphere fluid of 2048 atoms (FCC 8^3 x 4) at rho 0.8, T 1, forces
+    # straight from the cells every step; compared in 100-step segments, the
+    # oracle restarted from the GPU state each time
+    n = 2048
+    pos, vel, L = state(n, 0.8, 1.0, 1)
+    s = sim(pos, vel, L, skin=0.0, precision=prec, cell_list_only=True)
+    p, v = oracle.wrap(pos, L), vel
+    for seg in range(10):
+        ref = oracle.run(p, v, L, RC, 0.0, DT, 100)
+        s.step(100)
+        p, v = s.get_state()
+        f_rms = max(float(np.sqrt(np.mean(ref["f"] ** 2))), 1.0)
+        dv, dx = _trajectory_tol(prec, f_rms, 100)
+        assert np.sqrt(np.mean((v - ref["vel"]) ** 2)) <= dv, seg
+        assert np.sqrt(np.mean(min_image(p - ref["pos"], L) ** 2)) <= dx, seg
+    m = s.measure()
+    assert m["step"] == 1000 and m["rebuilds"] == 1000 + 1
+    s.close()
+
+
+def test_tiny_systems():
+    # one atom: no partners, zero force; two atoms across the boundary: the
+    # closed-form pair force
+    L = np.array([6.0, 6.0, 6.0])
+    for prec in PRECS:
+        s = sim(np.array([[0.1, 0.2, 0.3]]), np.array([[1.0, 0.0, 0.0]]), L, skin=0.4, precision=prec)
+        assert np.all(s.forces() == 0.0)
+        s.step(10)
+        p, v = s.get_state()
+        assert p[0, 0] == pytest.approx(0.1 + 10 * DT, abs=1e-6)
+        s.close()
+        pos = np.array([[-3.0 + 0.45, 0.1, -0.2], [3.0 - 0.45, 0.1, -0.2]])
+        s = sim(pos, np.zeros((2, 3)), L, skin=0.4, precision=prec)
+        fr, u = oracle.pair(0.81, 1.0)
+        f = s.forces()
+        assert f[0, 0] == pytest.approx(fr * 0.9, rel=FORCE_TOL[prec] * 10)
+        assert f[1, 0] == pytest.approx(-fr * 0.9, rel=FORCE_TOL[prec] * 10)
+        assert s.measure()["pe"] == pytest.approx(u, rel=1e-6)
+        s.close()
