@@ -64,6 +64,19 @@ def dist_env():
     return ws, rank, local
 
 
+def job_throughput(units_local, ms_local, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas: units summed over ranks,
+    divided by the slowest rank's time.  Returns (units/s, max ms)."""
+    if dist is None:
+        return units_local / (ms_local / 1e3), ms_local
+    import torch
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(u.item()) / (float(t.item()) / 1e3), float(t.item())
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -230,10 +243,6 @@ def run_ours(args):
         e1.synchronize()
         ms = e0.elapsed_time(e1)
         barrier()
-        if dist is not None:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
         return ms
 
     # ---- mixed form: the headline ----
@@ -246,12 +255,11 @@ def run_ours(args):
     m0 = sim.measure()
     clocks = Clocks(local)
     clocks.start()
-    ms = timed(sim, args.steps)
+    ms_local = timed(sim, args.steps)
     clk = clocks.stop()
     m1 = sim.measure()
     st1 = sim.kernel_stats()
-    atom_steps = n * args.chunk * args.steps * ws
-    value = atom_steps / (ms / 1e3)
+    value, ms = job_throughput(n * args.chunk * args.steps, ms_local, dist, "cuda")
     launches = st1["launches"] - st0["launches"]
 
     # ---- roofline of the force + integrate kernel (event-timed launches) ----
@@ -297,11 +305,8 @@ def run_ours(args):
             e2e_step()
         barrier()
         t = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([t], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        e2e = {"value": n * args.chunk * k_e2e * ws / t, "unit": UNIT,
+        e2e_value, _ = job_throughput(n * args.chunk * k_e2e, 1e3 * t, dist, "cuda")
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": int(hp.numel() * 8 + hv.numel() * 8),
                "d2h_bytes_per_step": int(op.numel() * 8 + ov.numel() * 8),
                "steps": k_e2e, "what": "md_set_state from pinned host memory, md_step(%d), "
@@ -316,13 +321,13 @@ def run_ours(args):
         k64 = max(2, args.steps // 4)
         for _ in range(max(1, args.warmup // 2)):
             s64.step(args.chunk)
-        ms64 = timed(s64, k64)
+        ms64_local = timed(s64, k64)
         s64.set_profiling(True)
         q0 = s64.kernel_stats()
         s64.step(args.chunk)
         q1 = s64.kernel_stats()
         s64.close()
-        v64 = n * args.chunk * k64 * ws / (ms64 / 1e3)
+        v64, ms64 = job_throughput(n * args.chunk * k64, ms64_local, dist, "cuda")
         kms64 = q1["step_kernel_ms"] - q0["step_kernel_ms"]
         kl64 = q1["step_kernel_launches"] - q0["step_kernel_launches"]
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,

@@ -5,11 +5,11 @@
  * molecular dynamics performance with a programmable graphics processor"
  * (arXiv 0911.5631) on one NVIDIA GB300 (sm_103a):
  *
- *   cell binning (Sec. 2.2, Sec. 4.2) -> neighbour list with a shell of
- *   thickness delta (Sec. 2.1, Sec. 2.4) -> pair forces, potential energy
- *   and virial from Eq. (1) (Sec. 2.4) -> velocity-Verlet ("leapfrog")
- *   integration with the delta/2 rebuild rule (Sec. 2.1, steps (a)-(e)),
- *   with periodic cell-order reordering of the atoms (Sec. 2.5).
+ *   cell binning (Sec. 3.2, Sec. 4.2) -> neighbour list with a shell of
+ *   thickness delta (Sec. 3.1, Sec. 3.4) -> pair forces, potential energy
+ *   and virial from Eq. (1) (Sec. 3.4) -> velocity-Verlet ("leapfrog")
+ *   integration with the delta/2 rebuild rule (Sec. 3.1, steps (a)-(e)),
+ *   with periodic cell-order reordering of the atoms (Sec. 3.5).
  *
  * Units are reduced MD units: sigma = epsilon = m = 1.  The region is a
  * rectangular periodic box centred at the origin.
@@ -64,17 +64,17 @@ extern "C" {
  * change fields as needed. */
 typedef struct md_params {
     int32_t precision;        /* MD_PREC_MIXED (default) or MD_PREC_FP64          */
-    int32_t reorder_interval; /* N_R of Sec. 5.4: atoms are put back into cell
+    int32_t reorder_interval; /* N_R of Sec. 5.5: atoms are put back into cell
                                  order at the first rebuild at least this many
                                  steps after the previous reorder; 0 = never.
                                  Default 100.                                  */
     int32_t cell_list_only;   /* 1: no neighbour list; every step re-bins the
                                  atoms and takes forces straight from the 27
-                                 cells around each atom (Sec. 2.1, cells only).
+                                 cells around each atom (Sec. 3.1, cells only).
                                  Requires skin == 0.  Default 0.               */
     int32_t even_cells;       /* 1: round each G_d down to an even number (the
                                  rule behind the cell counts of Tables 1 and 5).
-                                 Default 0: G_d = floor(L_d / r_n) (Sec. 2.1). */
+                                 Default 0: G_d = floor(L_d / r_n) (Sec. 3.1). */
     int32_t nbr_capacity;     /* initial neighbour slots per atom; 0 = estimate
                                  from density and r_n.  Grown automatically.   */
     int32_t use_graphs;       /* 1 (default): md_step replays CUDA graphs whose
@@ -86,7 +86,7 @@ typedef struct md_params {
     double ushift;            /* constant added to Eq. (1) for r < r_c.  NaN
                                  (default) = automatic: +1 (epsilon) when r_c is
                                  2^(1/6) to 1e-12 relative (the soft-sphere
-                                 potential of Sec. 2.1), else 0.               */
+                                 potential of Sec. 3.1), else 0.               */
     void* stream;             /* cudaStream_t to run on; NULL (default) = a
                                  stream created and owned by the handle.       */
     int64_t reserved[6];
@@ -138,14 +138,14 @@ typedef struct md_handle md_handle;
 void md_default_params(md_params* p);
 
 /* Plans geometry for a box of edges box[0..2], n atoms, cutoff rc, shell
- * thickness skin (r_n = rc + skin, Sec. 2.1) and time step dt.  Returns
+ * thickness skin (r_n = rc + skin, Sec. 3.1) and time step dt.  Returns
  * MD_EINVAL when n <= 0, n >= 2^26, rc <= 0, skin < 0, dt <= 0, a box edge
  * is not positive, some G_d < 3 (the 27-cell neighbourhood would alias), or
  * cell_list_only is set with skin != 0.  p may be NULL.  Needs no GPU. */
 int md_plan(const double box[3], int64_t n, double rc, double skin, double dt,
             const md_params* p, md_plan_t* out);
 
-/* Creates a simulation handle and allocates its device state (Sec. 2.1:
+/* Creates a simulation handle and allocates its device state (Sec. 3.1:
  * region, cutoff, shell, time step).  Same argument checks as md_plan;
  * MD_ENODEV / MD_ENOMEM / MD_ECUDA on device failure.  *out is NULL on
  * error. */
@@ -160,7 +160,7 @@ int md_create(const double box[3], int64_t n, double rc, double skin, double dt,
 int md_set_state(md_handle* h, const double* pos, const double* vel);
 int md_set_state_device(md_handle* h, const double* pos, const double* vel);
 
-/* Advances nsteps velocity-Verlet steps (Sec. 2.1 (a)-(e)).  The neighbour
+/* Advances nsteps velocity-Verlet steps (Sec. 3.1 (a)-(e)).  The neighbour
  * list is rebuilt on the device whenever the largest displacement since the
  * last build reaches skin/2 (every step in cell-list-only mode); atoms are
  * reordered into cell order every reorder_interval steps at a rebuild.  If
@@ -170,7 +170,7 @@ int md_set_state_device(md_handle* h, const double* pos, const double* vel);
 int md_step(md_handle* h, int64_t nsteps);
 
 /* Kinetic and potential energy, virial, pressure and counters of the
- * current state (Sec. 2.5 global reductions, Sec. 4.3), reduced on the
+ * current state (Sec. 3.5 global reductions, Sec. 4.3), reduced on the
  * device in FP64 in a fixed order (run-to-run deterministic). */
 int md_measure(md_handle* h, md_measure_t* out);
 
@@ -212,6 +212,13 @@ void md_destroy(md_handle* h);
 /* Message for the handle's last failure ("" if none); h may be NULL for
  * failures of md_create. */
 const char* md_last_error(const md_handle* h);
+
+/* Device self-check of the library's integer-pipe number conversions
+ * (binary32<->binary64, binary32<->int64 fixed point) against the hardware
+ * conversions on n hashed inputs (uses the current device).  failures[0..3]
+ * receive the mismatch counts for float->double, double->float,
+ * float->int64 and int64->float.  MD_ENODEV without a GPU. */
+int md_selftest(int64_t n, int64_t failures[4]);
 
 /* Static description of an error code. */
 const char* md_strerror(int code);

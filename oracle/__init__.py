@@ -10,14 +10,14 @@ contraction); this module compiles it with gcc on first use and wraps it with
 ctypes and numpy.  Every function follows a passage of Rapaport,
 arXiv 0911.5631:
 
-* ``pair``            -- Eq. (1) plus the soft-sphere shift (Sec. 2.1)
-* ``cell_grid``       -- G_d = floor(L_d / r_n) (Sec. 2.1); ``even=True``
+* ``pair``            -- Eq. (1) plus the soft-sphere shift (Sec. 3.1)
+* ``cell_grid``       -- G_d = floor(L_d / r_n) (Sec. 3.1); ``even=True``
                          reproduces the cell counts of Tables 1 and 5
-* ``wrap``/``cell_of``-- periodic wrap and cell assignment (Sec. 2.2, Sec. 4.2)
-* ``pairs_cells``     -- linked-list cells, half-shell enumeration (Sec. 2.2)
+* ``wrap``/``cell_of``-- periodic wrap and cell assignment (Sec. 3.2, Sec. 4.2)
+* ``pairs_cells``     -- linked-list cells, half-shell enumeration (Sec. 3.2)
 * ``pairs_brute``     -- O(N^2) minimum-image definition of the pair set
 * ``forces_cells`` / ``forces_brute`` / ``forces_sampled`` -- forces, U, W
-* ``run``             -- the step loop (a)-(f) of Sec. 2.1 with a skin-based
+* ``run``             -- the step loop (a)-(f) of Sec. 3.1 with a skin-based
                          neighbour list and the delta/2 rebuild rule
 """
 from __future__ import annotations
@@ -112,7 +112,7 @@ def _pos(p):
 
 def wca_shift(rc: float) -> float:
     """Shift added to Eq. (1): +epsilon for the soft-sphere cutoff 2^(1/6)
-    (Sec. 2.1), none for a plain truncated Lennard-Jones cutoff."""
+    (Sec. 3.1), none for a plain truncated Lennard-Jones cutoff."""
     return 1.0 if abs(rc - 2.0 ** (1.0 / 6.0)) <= 1e-12 * rc else 0.0
 
 

@@ -12,15 +12,15 @@
  *
  *   - pair potential: Eq. (1) (Lennard-Jones) truncated at r_c, plus a
  *     constant shift; the soft-sphere (SP, WCA) case is r_c = 2^(1/6) with a
- *     shift of +epsilon (Sec. 2.1).  Reduced units sigma = epsilon = m = 1.
+ *     shift of +epsilon (Sec. 3.1).  Reduced units sigma = epsilon = m = 1.
  *   - region: centred at the origin, edge L_d, cell grid G_d = floor(L_d/r_n),
- *     cell width w_d = L_d/G_d (Sec. 2.1); optional rounding of G_d down to
+ *     cell width w_d = L_d/G_d (Sec. 3.1); optional rounding of G_d down to
  *     an even number, which is what every cell count printed in Tables 1
  *     and 5 corresponds to.
  *   - cell assignment by linked lists and the half-shell (14 offsets) pair
- *     enumeration with periodic-image shifts beta (Sec. 2.2).
- *   - pair-list force evaluation using Newton's third law (Sec. 2.2).
- *   - the step loop (a)-(f) of Sec. 2.1: half kick + drift; periodic wrap
+ *     enumeration with periodic-image shifts beta (Sec. 3.2).
+ *   - pair-list force evaluation using Newton's third law (Sec. 3.2).
+ *   - the step loop (a)-(f) of Sec. 3.1: half kick + drift; periodic wrap
  *     and rebuild when the largest displacement since the last rebuild
  *     reaches delta/2; forces; half kick; properties; optional velocity
  *     rescaling during equilibration.
@@ -52,7 +52,7 @@ void orc_pair(double r2, double ushift, double* fr, double* u)
 }
 
 /* ------------------------------------------------------------------ */
-/* Region and cells (Sec. 2.1, Sec. 2.2)                               */
+/* Region and cells (Sec. 3.1, Sec. 3.2)                               */
 /* ------------------------------------------------------------------ */
 
 /* G_d = floor(L_d / r_n); with even != 0 rounded down to an even count.
@@ -146,14 +146,14 @@ static int pl_push(pairlist_t* pl, int32_t i, int32_t j, const int s[3])
 }
 
 /* The 14 cell offsets of the half shell: the cell itself and 13 of its 26
- * neighbours, one from each +/- pair (Sec. 2.2). */
+ * neighbours, one from each +/- pair (Sec. 3.2). */
 static const int HALF_SHELL[14][3] = {
     {0, 0, 0},  {1, 0, 0},  {1, 1, 0},  {0, 1, 0},  {-1, 1, 0},
     {0, 0, 1},  {1, 0, 1},  {1, 1, 1},  {0, 1, 1},  {-1, 1, 1},
     {-1, 0, 1}, {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}};
 
 /* Linked-list cell assignment and half-shell pair enumeration with cutoff
- * rcut (Sec. 2.2).  Positions must lie in [-L/2, L/2).  Each pair with
+ * rcut (Sec. 3.2).  Positions must lie in [-L/2, L/2).  Each pair with
  * |r_i - r_j + b| < rcut is recorded once together with its shift b. */
 static int build_pairs_cells(int64_t n, const double* pos, const double L[3], const int G[3],
                              double rcut, pairlist_t* pl)
@@ -277,7 +277,7 @@ double orc_pair_r2(const double* pos, const double L[3], int64_t i, int64_t j)
 /* Forces, energy, virial                                              */
 /* ------------------------------------------------------------------ */
 
-/* Pair-list force evaluation with Newton's third law (Sec. 2.2): each listed
+/* Pair-list force evaluation with Newton's third law (Sec. 3.2): each listed
  * pair within rc adds fr * r to atom i and subtracts it from atom j.
  * U = sum u(r); W = sum r . f over pairs. */
 static void forces_from_pairs(int64_t n, const double* pos, const double L[3], const pairlist_t* pl,
@@ -396,7 +396,7 @@ int64_t orc_neighbors_of(int64_t n, const double* pos, const double L[3], double
 }
 
 /* ------------------------------------------------------------------ */
-/* The MD loop (Sec. 2.1, steps (a)-(f))                               */
+/* The MD loop (Sec. 3.1, steps (a)-(f))                               */
 /* ------------------------------------------------------------------ */
 
 typedef struct {

@@ -131,6 +131,7 @@ SIGNATURES = [
     ("md_sync", C.c_int, [_H]),
     ("md_destroy", None, [_H]),
     ("md_last_error", C.c_char_p, [_H]),
+    ("md_selftest", C.c_int, [C.c_int64, C.POINTER(C.c_int64)]),
     ("md_strerror", C.c_char_p, [C.c_int]),
 ]
 
@@ -281,6 +282,12 @@ def md_destroy(h):
 def md_last_error(h=None) -> str:
     s = lib().md_last_error(h)
     return s.decode() if s else ""
+
+
+def md_selftest(n=1 << 22):
+    f = (C.c_int64 * 4)()
+    _check(lib().md_selftest(int(n), f))
+    return list(f)
 
 
 def md_strerror(code) -> str:

@@ -78,6 +78,7 @@ int resolve_plan(const double box[3], int64_t n, double rc, double skin, double 
         int G = (int)g;
         if (p->even_cells) G -= G % 2;
         if (G < 3) return fail("box edge below 3 r_n: the 27-cell neighbourhood would alias");
+        if (G > 1023) return fail("more than 1023 cells along one edge");
         out->G[k] = G;
         out->w[k] = box[k] / G;
         nc *= G;
@@ -102,7 +103,8 @@ int resolve_plan(const double box[3], int64_t n, double rc, double skin, double 
         }
         cap = (cap + 3) & ~3;
         if (cap < 8) cap = 8;
-        if (cap > 4096) cap = 4096;
+        int cap_max = p->precision == MD_PREC_MIXED ? md::kMaxCapMixed : 4096;
+        if (cap > cap_max) cap = cap_max;
     }
     out->nbr_capacity = cap;
     // device bytes: see Sim::allocate
@@ -110,7 +112,8 @@ int resolve_plan(const double box[3], int64_t n, double rc, double skin, double 
     int64_t real_b = p->precision == MD_PREC_FP64 ? 8 : 4;
     int64_t pos4_b = p->precision == MD_PREC_FP64 ? 32 : 16;
     int64_t per_atom = 3 * 4 /*cell perm rank*/ + 3 * real_b /*pb*/ + 24 /*o*/ + 3 * real_b /*v*/ +
-                       3 * real_b /*f*/ + 3 * pos4_b /*pA pB cand*/ + 8 + 3 * real_b + 24 + 3 * real_b /*scratch*/ +
+                       3 * real_b /*f*/ + 2 * pos4_b /*pA pB*/ + 16 /*cand*/ + 8 + 3 * real_b + 24 +
+                       3 * real_b /*scratch*/ +
                        4 /*order*/ + 4 /*nn*/ + 48 /*io*/;
     int64_t ncol = (n + 31) / 32 * 32;
     out->device_bytes = per_atom * n + ncol * cap * 4 + (2 * nc + 1) * 4 + ((nc + kScanTile - 1) / kScanTile) * 4 +
@@ -246,6 +249,7 @@ struct Sim : SimBase {
             a.invW[k] = (double)plan.G[k] / box[k];
             a.w[k] = plan.w[k];
             a.hw[k] = 0.5 * plan.w[k];
+            a.hwf_in[k] = (float)(0.5 * plan.w[k] * (1.0 - 1e-6));
             a.wf[k] = (float)plan.w[k];
         }
         a.ntiles = (int)((plan.n_cells + kScanTile - 1) / kScanTile);
@@ -333,11 +337,14 @@ struct Sim : SimBase {
         return (unsigned)((m + kBlock - 1) / kBlock);
     }
 
-    void* step_fn() const { return prm.cell_list_only ? kt.step_cells : kt.step_list; }
+    void* step_fn(bool final_node) const {
+        if (prm.cell_list_only) return final_node ? kt.step_cells_final : kt.step_cells;
+        return final_node ? kt.step_list_final : kt.step_list;
+    }
 
-    // The rebuild branch, as stream launches with the device-flag guard.
-    int rebuild_eager() {
-        int g = 1;
+    // The rebuild branch as stream launches.  guard = 1: every kernel returns
+    // at once unless the device rebuild flag is set.
+    int rebuild_eager(int g = 1) {
         MD_CUDA(launch(kt.bin, grid_atoms(), kBlock, a, g));
         MD_CUDA(launch(kt.scan_tiles, (unsigned)a.ntiles, kBlock, a, g));
         MD_CUDA(launch(kt.scan_top, 1, 1024, a, g));
@@ -351,10 +358,10 @@ struct Sim : SimBase {
         return MD_OK;
     }
 
-    int step_kernel_eager(int mode) {
+    int step_kernel_eager(int mode, bool final_node) {
         cudaGraphConditionalHandle none = 0;
         int has = 0;
-        MD_CUDA(launch(step_fn(), grid_atoms(), kBlock, a, mode, none, has));
+        MD_CUDA(launch(step_fn(final_node), grid_atoms(), kBlock, a, mode, none, has));
         return MD_OK;
     }
 
@@ -428,7 +435,8 @@ struct Sim : SimBase {
             if (r) return r;
             cudaGraphConditionalHandle nxt = (s + 1 < K) ? h[s + 1] : 0;
             int has = (s + 1 < K) ? 1 : 0;
-            MD_CUDA(add_kernel(c.g, &ifn, &node, step_fn(), grid_atoms(), kBlock, a, mode, nxt, has));
+            // only a graph's last node can meet the last step of a call
+            MD_CUDA(add_kernel(c.g, &ifn, &node, step_fn(s + 1 == K), grid_atoms(), kBlock, a, mode, nxt, has));
             prev = node;
         }
         MD_CUDA(cudaGraphInstantiate(&c.e, c.g, 0));
@@ -476,11 +484,17 @@ struct Sim : SimBase {
                     ev.push_back(e);
                 }
             }
+            // Stream launches: the host reads the device rebuild flag before
+            // each step, so only rebuilds that are due are launched (one
+            // round trip per step; this path serves profiling and checks).
             for (int64_t s = 0; s < nsteps; s++) {
-                int r = rebuild_eager();
+                int flag = 0;
+                MD_CUDA(cudaMemcpyAsync(&flag, &a.ctr->rebuild_flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
+                MD_CUDA(cudaStreamSynchronize(stream));
+                int r = flag ? rebuild_eager(0) : MD_OK;
                 if (r) return r;
                 if (profiling) MD_CUDA(cudaEventRecord(ev[2 * s], stream));
-                r = step_kernel_eager(kModeAuto);
+                r = step_kernel_eager(kModeAuto, s + 1 == nsteps);
                 if (r) return r;
                 if (profiling) MD_CUDA(cudaEventRecord(ev[2 * s + 1], stream));
             }
@@ -505,6 +519,10 @@ struct Sim : SimBase {
     }
 
     int check_fatal(const Counters& c) {
+        if (c.error & kErrInternal) {
+            err = "internal: a step kernel without the final-step path met the last step of a call";
+            return MD_ECUDA;
+        }
         if (c.error & (kErrUnstable | kErrClose)) {
             err = (c.error & kErrClose) ? "two atoms came closer than the fixed-point force range allows"
                                         : "non-finite coordinate or an atom moved more than one cell between rebuilds";
@@ -518,10 +536,12 @@ struct Sim : SimBase {
         int need = c.need_cap > a.cap ? c.need_cap : a.cap + 4;
         int cap = (int)std::ceil(need * 1.25) + 4;
         cap = (cap + 3) & ~3;
-        if (cap > 8192) {
-            err = "neighbour capacity would exceed 8192 entries per atom";
+        int cap_max = P::kFp64 ? 8192 : kMaxCapMixed;
+        if (need > cap_max) {
+            err = "an atom has more neighbours than the largest list capacity";
             return MD_EOVERFLOW;
         }
+        if (cap > cap_max) cap = cap_max;
         MD_CUDA(cudaStreamSynchronize(stream));
         destroy_graphs();
         int r = alloc_nbr(cap);
@@ -582,7 +602,7 @@ struct Sim : SimBase {
             r = regrow(c);
             if (r) return r;
         }
-        r = step_kernel_eager(kModeInit);
+        r = step_kernel_eager(kModeInit, true);
         if (r) return r;
         Counters c;
         r = read_counters(&c);
@@ -851,59 +871,59 @@ int md_create(const double box[3], int64_t n, double rc, double skin, double dt,
     return MD_OK;
 }
 
-#define MD_H(h) \
+#define MD_HANDLE_CHECK(h) \
     if (!(h) || !(h)->sim) return MD_EINVAL
 
 int md_set_state(md_handle* h, const double* pos, const double* vel) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->set_state(pos, vel, false);
 }
 int md_set_state_device(md_handle* h, const double* pos, const double* vel) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->set_state(pos, vel, true);
 }
 int md_step(md_handle* h, int64_t nsteps) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->step(nsteps);
 }
 int md_measure(md_handle* h, md_measure_t* out) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->measure(out);
 }
 int md_get_state(md_handle* h, double* pos, double* vel) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->get_state(pos, vel, false);
 }
 int md_get_state_device(md_handle* h, double* pos, double* vel) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->get_state(pos, vel, true);
 }
 int md_get_forces(md_handle* h, double* f) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->get_forces(f);
 }
 int md_debug_cells(md_handle* h, int32_t* cell) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->debug_cells(cell);
 }
 int md_debug_neighbors(md_handle* h, int64_t* count, int64_t* entries, int32_t* pairs, int64_t capacity) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->debug_neighbors(count, entries, pairs, capacity);
 }
 int md_get_plan(md_handle* h, md_plan_t* out) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->get_plan(out);
 }
 int md_set_profiling(md_handle* h, int on) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->set_profiling(on);
 }
 int md_kernel_stats(md_handle* h, md_kernel_stats_t* out) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->kernel_stats(out);
 }
 int md_sync(md_handle* h) {
-    MD_H(h);
+    MD_HANDLE_CHECK(h);
     return h->sim->sync();
 }
 void md_destroy(md_handle* h) {
@@ -915,6 +935,32 @@ const char* md_last_error(const md_handle* h) {
     if (!h || !h->sim) return g_create_error.c_str();
     return h->sim->err.c_str();
 }
+int md_selftest(int64_t n, int64_t failures[4]) {
+    if (n <= 0 || !failures) return MD_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return MD_ENODEV;
+    }
+    KernelTable<Mixed> kt = make_kernel_table<Mixed>();
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, 4 * sizeof(unsigned long long)) != cudaSuccess) return MD_ENOMEM;
+    cudaMemset(d, 0, 4 * sizeof(unsigned long long));
+    long long nn = (long long)n;
+    void* args[] = {&nn, &d};
+    unsigned grid = (unsigned)((n + kBlock - 1) / kBlock);
+    cudaError_t e = cudaLaunchKernel(kt.selftest, dim3(grid), dim3(kBlock), args, 0, 0);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        g_create_error = cudaGetErrorString(e);
+        return MD_ECUDA;
+    }
+    for (int k = 0; k < 4; k++) failures[k] = (int64_t)h[k];
+    return MD_OK;
+}
+
 const char* md_strerror(int code) {
     switch (code) {
         case MD_OK: return "ok";

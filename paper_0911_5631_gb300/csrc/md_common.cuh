@@ -11,9 +11,12 @@ namespace md {
 constexpr int kBlock = 256;
 // Elements per block of the cell-count scan (kBlock threads x 8).
 constexpr int kScanTile = 2048;
+// Largest neighbour capacity of the mixed form (its fixed-point partial
+// sums stay inside int32 for up to this many terms).
+constexpr int kMaxCapMixed = 512;
 // Neighbour entries are j | code << kCodeShift; code packs the cell offset
 // (d_x+1) | (d_y+1) << 2 | (d_z+1) << 4 of j's cell relative to i's cell, the
-// periodic-image information beta of Sec. 2.2 in 6 high bits.
+// periodic-image information beta of Sec. 3.2 in 6 high bits.
 constexpr int kCodeShift = 26;
 constexpr int kIndexMask = (1 << kCodeShift) - 1;
 constexpr int64_t kMaxAtoms = int64_t(1) << kCodeShift;
@@ -28,6 +31,7 @@ enum : int {
     kErrOverflow = 1,   // neighbour list longer than its capacity
     kErrUnstable = 2,   // atom left its cell neighbourhood / non-finite value
     kErrClose = 4,      // pair closer than the fixed-point range allows
+    kErrInternal = 8,   // a plain step node met the last step of a call
 };
 
 // Step-kernel modes.
@@ -92,6 +96,7 @@ struct Args {
     double L[3], hL[3], invL[3], invW[3];
     double w[3];        // cell widths
     double hw[3];       // half cell widths
+    float hwf_in[3];    // FP32 bound below which an offset is surely inside its cell
     float wf[3];
     double dt, h;       // time step and half step
     float dtf, hf;
@@ -115,7 +120,7 @@ struct Args {
     vel* vx; vel* vy; vel* vz;
     real* fx; real* fy; real* fz;      // forces of the last completed step
     pos4* pA; pos4* pB;                // current cell-relative coordinates (ping-pong)
-    pos4* cand;                        // coordinates in cell order + storage index
+    float4* cand;                      // FP32 coordinates in cell order + storage index
 
     // reorder scratch (same shapes as the state)
     int* s_cell; int* s_perm;

@@ -1,19 +1,25 @@
 // md_kernels.cuh -- sm_103a kernels of the soft-sphere MD hot path.
 //
 // One thread per atom (or per cell-ordered slot) throughout, as in the
-// paper's GPU formulation (Sec. 2.4: one neighbour column per atom, no use
+// paper's GPU formulation (Sec. 3.4: one neighbour column per atom, no use
 // of Newton's third law; Sec. 4.2: atom identity from block and thread
 // indices).  Included by one translation unit per precision form.
 //
 // Coordinates.  Every atom belongs to a cell (c_x, c_y, c_z) of width w_d
-// (Sec. 2.1).  Its position is the cell centre plus an offset pb (fixed
+// (Sec. 3.1).  Its position is the cell centre plus an offset pb (fixed
 // between rebuilds, FP32 in the mixed form, FP64 in the FP64 form) plus a
 // displacement o (FP64) accumulated since the last rebuild.  The pair
 // coordinate every other atom reads is pb + o rounded to the pair precision;
 // for a neighbour whose cell lies at offset d (components in {-1, 0, 1},
 // periodic wrap included) the separation is (p_i - p_j) - d w, so no
 // coordinate of magnitude L ever enters the FP32 arithmetic and |o| is the
-// exact displacement used by the skin/2 rebuild rule (Sec. 2.1).
+// exact displacement used by the skin/2 rebuild rule (Sec. 3.1).
+//
+// GB300 note.  The FP64 pipe issues about two instructions per clock per SM
+// here, and so do the hardware conversions float<->int64 and
+// double<->float.  The mixed form therefore keeps FP64 to the three
+// position-update FMAs per atom and step, and does its conversions on the
+// FP32 and integer pipes (namespace cvt, struct Fix).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -32,8 +38,8 @@ __device__ __forceinline__ int64_t gtid() {
     return (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
 }
 
-// Set by the last block of a grid to finish, after every other block has
-// passed the point of its call.  All threads of the block must call it.
+// True in the last block of the grid to get here, after every other block
+// has passed the same point.  All threads of the block must call it.
 __device__ __forceinline__ bool last_block_done(Counters* C) {
     __shared__ int s_last;
     __syncthreads();
@@ -91,11 +97,21 @@ __device__ __forceinline__ int block_max_int(int v, int* sh) {
     return s;
 }
 
-__device__ __forceinline__ void decode_cell(int c, const int G[3], int& cx, int& cy, int& cz) {
-    cx = c % G[0];
-    int r = c / G[0];
-    cy = r % G[1];
-    cz = r / G[1];
+// Cell coordinates are stored packed, 10 bits each (G_d <= 1023).
+__device__ __forceinline__ int pack_cell(int cx, int cy, int cz) { return cx | (cy << 10) | (cz << 20); }
+__device__ __forceinline__ void unpack_cell(int p, int& cx, int& cy, int& cz) {
+    cx = p & 1023;
+    cy = (p >> 10) & 1023;
+    cz = (p >> 20) & 1023;
+}
+// Scalar cell index c = (c_z G_y + c_y) G_x + c_x (0-based form of Sec. 3.1).
+__device__ __forceinline__ int linear_cell(int cx, int cy, int cz, const int G[3]) {
+    return (cz * G[1] + cy) * G[0] + cx;
+}
+__device__ __forceinline__ int linear_of_packed(int p, const int G[3]) {
+    int cx, cy, cz;
+    unpack_cell(p, cx, cy, cz);
+    return linear_cell(cx, cy, cz, G);
 }
 
 __device__ __forceinline__ int wrap_add(int c, int d, int G) {
@@ -111,22 +127,117 @@ __device__ __forceinline__ T code_shift(unsigned k, T w) {
     return k == 0u ? w : (k == 2u ? -w : T(0));
 }
 
+// ---------------------------------------------------------------------------
+// Conversions on the FP32 and integer pipes.  They follow the IEEE 754
+// binary32/binary64 encodings with round-to-nearest-even; values below the
+// binary32 normal range are flushed to signed zero, which the coordinates
+// and forces here never reach.  md_selftest compares them with the hardware
+// conversions.
+// ---------------------------------------------------------------------------
+namespace cvt {
+
+// binary32 -> binary64 (exact).
+__device__ __forceinline__ double f64(float x) {
+    unsigned b = __float_as_uint(x);
+    unsigned s = b & 0x80000000u;
+    unsigned e = (b >> 23) & 0xFFu;
+    unsigned m = b & 0x7FFFFFu;
+    unsigned hi = s | ((e + 896u) << 20) | (m >> 3);
+    unsigned lo = m << 29;
+    if (e == 0u) { hi = s; lo = 0u; }
+    if (e == 255u) hi = s | 0x7FF00000u | (m >> 3) | (m ? 0x80000u : 0u);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// binary64 -> binary32, round to nearest, ties to even.
+__device__ __forceinline__ float f32(double x) {
+    unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    unsigned s = hi & 0x80000000u;
+    int E = (int)((hi >> 20) & 0x7FFu);
+    int e = E - 896;
+    unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    unsigned rest = lo & 0x1FFFFFFFu;
+    unsigned f = s | ((unsigned)e << 23) | m;
+    f += (unsigned)((rest > 0x10000000u) | ((rest == 0x10000000u) & (m & 1u)));
+    if (e <= 0) f = s;
+    if (e >= 255) f = s | 0x7F800000u | ((E == 0x7FF && ((hi & 0xFFFFFu) | lo)) ? 0x400000u : 0u);
+    return __uint_as_float(f);
+}
+
+// int64 -> binary32, round to nearest, ties to even.
+__device__ __forceinline__ float from_fix(long long q) {
+    unsigned long long mag = q < 0 ? 0ull - (unsigned long long)q : (unsigned long long)q;
+    if (mag == 0ull) return 0.0f;
+    int lz = __clzll((long long)mag);
+    unsigned long long nrm = mag << lz;
+    unsigned m = (unsigned)(nrm >> 40);
+    unsigned long long rest = nrm & 0xFFFFFFFFFFull;
+    unsigned f = ((unsigned)(190 - lz) << 23) + (m & 0x7FFFFFu);
+    f += (unsigned)((rest > 0x8000000000ull) | ((rest == 0x8000000000ull) & (m & 1u)));
+    return __uint_as_float(f | (q < 0 ? 0x80000000u : 0u));
+}
+
+}  // namespace cvt
+
+// Fixed point with scale 2^32 kept as three int32 partial sums.
+// add(g) adds round(g 2^32) (ties to even) for |g| < 2^30 as
+// a 2^44 + b 2^22 + c with |a| <= 2^18, |b|, |c| <= 2^21: each chunk is
+// rounded to an integer by adding 1.5 2^23 in FP32, and every remainder is
+// exact, so the three sums are exact and independent of the order of the
+// terms, and add(-g) subtracts exactly what add(g) adds.  value()
+// assembles the int64 sum.  With at most 512 terms no partial sum leaves
+// int32.
+struct Fix {
+    int a = 0, b = 0, c = 0;
+    __device__ __forceinline__ void add(float g) {
+        const float M = 12582912.0f;  // 1.5 * 2^23
+        const int MB = 0x4B400000;    // its bit pattern
+        float s1 = fmaf(g, 0x1p-12f, M);
+        a += __float_as_int(s1) - MB;
+        float r1 = fmaf(s1 - M, -4096.0f, g);
+        float s2 = fmaf(r1, 1024.0f, M);
+        b += __float_as_int(s2) - MB;
+        float r2 = fmaf(s2 - M, -0x1p-10f, r1);
+        float s3 = fmaf(r2, 4294967296.0f, M);
+        c += __float_as_int(s3) - MB;
+    }
+    __device__ __forceinline__ long long value() const {
+        return (long long)a * (1ll << 44) + (long long)b * (1ll << 22) + (long long)c;
+    }
+};
+
 // Pair coordinate of one component from build offset and displacement.
-__device__ __forceinline__ float pair_coord(float pb, double o) { return pb + __double2float_rn(o); }
+__device__ __forceinline__ float pair_coord(float pb, double o) { return pb + cvt::f32(o); }
 __device__ __forceinline__ double pair_coord(double pb, double o) { return __dadd_rn(pb, o); }
 
 // FP64 cell-relative offset (build offset + displacement).
-__device__ __forceinline__ double full_offset(float pb, double o) { return __dadd_rn((double)pb, o); }
+__device__ __forceinline__ double full_offset(float pb, double o) { return __dadd_rn(cvt::f64(pb), o); }
 __device__ __forceinline__ double full_offset(double pb, double o) { return __dadd_rn(pb, o); }
 
 // Split an FP64 cell-relative offset t into (pb, o) with pb + o == t.
 __device__ __forceinline__ void split_offset(double t, float& pb, double& o) {
-    pb = __double2float_rn(t);
-    o = __dsub_rn(t, (double)pb);  // exact: pb is t rounded
+    pb = cvt::f32(t);
+    o = __dsub_rn(t, cvt::f64(pb));  // exact: pb is t rounded
 }
 __device__ __forceinline__ void split_offset(double t, double& pb, double& o) {
     pb = t;
     o = 0.0;
+}
+
+// Drift of one displacement component: o += v dt in FP64.
+__device__ __forceinline__ double drift(double o, float v, double dt) { return fma(cvt::f64(v), dt, o); }
+__device__ __forceinline__ double drift(double o, double v, double dt) { return fma(v, dt, o); }
+
+// Pair coordinate after a drift and the squared displacement in the pair
+// precision (the skin/2 test).
+__device__ __forceinline__ float moved(float pb, double o, float& p) {
+    float d = cvt::f32(o);
+    p = pb + d;
+    return d * d;
+}
+__device__ __forceinline__ double moved(double pb, double o, double& p) {
+    p = __dadd_rn(pb, o);
+    return o * o;
 }
 
 __device__ __forceinline__ float4 make_pos4(float x, float y, float z, int j) {
@@ -135,56 +246,53 @@ __device__ __forceinline__ float4 make_pos4(float x, float y, float z, int j) {
 __device__ __forceinline__ double4_32a make_pos4(double x, double y, double z, int j) {
     return make_double4_32a(x, y, z, __longlong_as_double((long long)j));
 }
-__device__ __forceinline__ int pos4_index(float4 p) { return __float_as_int(p.w); }
-__device__ __forceinline__ int pos4_index(double4_32a p) { return (int)__double_as_longlong(p.w); }
-
 __device__ __forceinline__ float4 ld_pos4(const float4* p) { return __ldg(p); }
 __device__ __forceinline__ double4_32a ld_pos4(const double4_32a* p) {
     const double2* q = reinterpret_cast<const double2*>(p);
     double2 a = __ldg(q), b = __ldg(q + 1);
     return make_double4_32a(a.x, a.y, b.x, b.y);
 }
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return cvt::f32(x); }
 
 // ---------------------------------------------------------------------------
-// pair term, Eq. (1) + shift.  Accumulators per precision form.
+// pair term, Eq. (1) + shift, and the per-atom accumulators
 // ---------------------------------------------------------------------------
 
-// Mixed form: FP32 pair arithmetic; per-atom sums in int64 fixed point
-// (scale 2^32) so the result does not depend on the order of the pairs.
+// Mixed form: FP32 pair arithmetic; per-atom sums in int64 fixed point.
 struct AccMixed {
-    long long fx = 0, fy = 0, fz = 0, u = 0, w = 0;
+    Fix fx, fy, fz, u, w;
     int close = 0;
-    __device__ __forceinline__ void pair(const Args<Mixed>& a, float dx, float dy, float dz,
-                                         bool energy) {
+    template <bool kEnergy>
+    __device__ __forceinline__ void pair(const Args<Mixed>& a, float dx, float dy, float dz) {
         float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (r2 < a.rc2f) {
             close |= (r2 < a.close2f);
             float ir2 = __frcp_rn(r2);
             float ir6 = ir2 * ir2 * ir2;
-            // 48 * 2^32 is exact in FP32; the scale rides on the force factor
-            float frs = (48.0f * kFixScaleF) * ir6 * (ir6 - 0.5f) * ir2;
-            fx += __float2ll_rn(frs * dx);
-            fy += __float2ll_rn(frs * dy);
-            fz += __float2ll_rn(frs * dz);
-            if (energy) {
-                u += __float2ll_rn(kFixScaleF * fmaf(4.0f * ir6, ir6 - 1.0f, a.ushiftf));
-                w += __float2ll_rn(frs * r2);
+            float fr = 48.0f * ir6 * (ir6 - 0.5f) * ir2;
+            fx.add(fr * dx);
+            fy.add(fr * dy);
+            fz.add(fr * dz);
+            if constexpr (kEnergy) {
+                u.add(fmaf(4.0f * ir6, ir6 - 1.0f, a.ushiftf));
+                w.add(fr * r2);
             }
         }
     }
-    __device__ __forceinline__ float force_x() const { return (float)fx * kFixInvF; }
-    __device__ __forceinline__ float force_y() const { return (float)fy * kFixInvF; }
-    __device__ __forceinline__ float force_z() const { return (float)fz * kFixInvF; }
-    __device__ __forceinline__ double energy() const { return (double)u * kFixInv; }
-    __device__ __forceinline__ double virial() const { return (double)w * kFixInv; }
+    __device__ __forceinline__ float force_x() const { return cvt::from_fix(fx.value()) * kFixInvF; }
+    __device__ __forceinline__ float force_y() const { return cvt::from_fix(fy.value()) * kFixInvF; }
+    __device__ __forceinline__ float force_z() const { return cvt::from_fix(fz.value()) * kFixInvF; }
+    __device__ __forceinline__ double energy() const { return (double)u.value() * kFixInv; }
+    __device__ __forceinline__ double virial() const { return (double)w.value() * kFixInv; }
 };
 
 // FP64 form: everything in double, summed in list order.
 struct AccF64 {
     double fx = 0, fy = 0, fz = 0, u = 0, w = 0;
     int close = 0;
-    __device__ __forceinline__ void pair(const Args<F64>& a, double dx, double dy, double dz,
-                                         bool energy) {
+    template <bool kEnergy>
+    __device__ __forceinline__ void pair(const Args<F64>& a, double dx, double dy, double dz) {
         double r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < a.rc2) {
             close |= (r2 < a.close2);
@@ -194,7 +302,7 @@ struct AccF64 {
             fx += fr * dx;
             fy += fr * dy;
             fz += fr * dz;
-            if (energy) {
+            if constexpr (kEnergy) {
                 u += 4.0 * ir6 * (ir6 - 1.0) + a.ushift;
                 w += fr * r2;
             }
@@ -211,22 +319,22 @@ template <class P> struct AccOf;
 template <> struct AccOf<Mixed> { using type = AccMixed; };
 template <> struct AccOf<F64> { using type = AccF64; };
 
-// Forces on atom i from its neighbour-list column (Sec. 2.4: W_{m,i}, m_i).
+// Forces on atom i from its neighbour-list column (Sec. 3.4: W_{m,i}, m_i).
 // Entries are read four at a time so several independent loads are in
 // flight per thread.
-template <class P>
+template <class P, bool kEnergy>
 __device__ __forceinline__ void forces_from_list(const Args<P>& a, int i, typename P::real qx,
                                                  typename P::real qy, typename P::real qz,
                                                  const typename P::pos4* __restrict__ pc,
-                                                 bool energy, typename AccOf<P>::type& acc) {
+                                                 typename AccOf<P>::type& acc) {
     using real = typename P::real;
     using pos4 = typename P::pos4;
     const int cnt = a.nn[i];
     const unsigned nlast = (unsigned)(a.n - 1);  // entries are always < n; the clamp only guards memory
     const int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
-    const real wx = (real)(P::kFp64 ? a.w[0] : a.wf[0]);
-    const real wy = (real)(P::kFp64 ? a.w[1] : a.wf[1]);
-    const real wz = (real)(P::kFp64 ? a.w[2] : a.wf[2]);
+    real wx, wy, wz;
+    if constexpr (P::kFp64) { wx = a.w[0]; wy = a.w[1]; wz = a.w[2]; }
+    else { wx = a.wf[0]; wy = a.wf[1]; wz = a.wf[2]; }
     for (int m = 0; m < cnt; m += 4) {
         unsigned e[4];
         pos4 pj[4];
@@ -243,25 +351,27 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int i, typena
                 real dx = (qx - pj[k].x) + code_shift<real>(code & 3u, wx);
                 real dy = (qy - pj[k].y) + code_shift<real>((code >> 2) & 3u, wy);
                 real dz = (qz - pj[k].z) + code_shift<real>((code >> 4) & 3u, wz);
-                acc.pair(a, dx, dy, dz, energy);
+                acc.template pair<kEnergy>(a, dx, dy, dz);
             }
         }
     }
 }
 
 // Forces on atom i straight from the 27 cells around its cell (cell-list
-// only variant; candidates read from the cell-ordered copy).
-template <class P>
+// only variant).  Candidates come from the cell-ordered copy; their pair
+// coordinates are read from the current buffer (FP64 form) or the copy
+// itself (mixed form, where the two hold the same numbers).
+template <class P, bool kEnergy>
 __device__ __forceinline__ void forces_from_cells(const Args<P>& a, int i, typename P::real qx,
                                                   typename P::real qy, typename P::real qz,
-                                                  bool energy, typename AccOf<P>::type& acc) {
+                                                  const typename P::pos4* __restrict__ pc,
+                                                  typename AccOf<P>::type& acc) {
     using real = typename P::real;
-    using pos4 = typename P::pos4;
     int cx, cy, cz;
-    decode_cell(a.cell[i], a.G, cx, cy, cz);
-    const real wx = (real)(P::kFp64 ? a.w[0] : a.wf[0]);
-    const real wy = (real)(P::kFp64 ? a.w[1] : a.wf[1]);
-    const real wz = (real)(P::kFp64 ? a.w[2] : a.wf[2]);
+    unpack_cell(a.cell[i], cx, cy, cz);
+    real wx, wy, wz;
+    if constexpr (P::kFp64) { wx = a.w[0]; wy = a.w[1]; wz = a.w[2]; }
+    else { wx = a.wf[0]; wy = a.wf[1]; wz = a.wf[2]; }
     for (int dz = -1; dz <= 1; dz++) {
         int z = wrap_add(cz, dz, a.G[2]);
         real sz = -(real)dz * wz;
@@ -271,12 +381,20 @@ __device__ __forceinline__ void forces_from_cells(const Args<P>& a, int i, typen
             for (int dx = -1; dx <= 1; dx++) {
                 int x = wrap_add(cx, dx, a.G[0]);
                 real sx = -(real)dx * wx;
-                int c2 = (z * a.G[1] + y) * a.G[0] + x;
+                int c2 = linear_cell(x, y, z, a.G);
                 int beg = a.cell_start[c2], end = min(a.cell_start[c2 + 1], (int)a.n);
                 for (int t = beg; t < end; t++) {
-                    pos4 pj = ld_pos4(a.cand + t);
-                    if (pos4_index(pj) == i) continue;
-                    acc.pair(a, (qx - pj.x) + sx, (qy - pj.y) + sy, (qz - pj.z) + sz, energy);
+                    float4 cj = __ldg(a.cand + t);
+                    int j = __float_as_int(cj.w);
+                    if (j == i) continue;
+                    real px, py, pz;
+                    if constexpr (P::kFp64) {
+                        auto pj = ld_pos4(pc + min((unsigned)j, (unsigned)(a.n - 1)));
+                        px = pj.x; py = pj.y; pz = pj.z;
+                    } else {
+                        px = cj.x; py = cj.y; pz = cj.z;
+                    }
+                    acc.template pair<kEnergy>(a, (qx - px) + sx, (qy - py) + sy, (qz - pz) + sz);
                 }
             }
         }
@@ -293,7 +411,6 @@ __device__ __forceinline__ void forces_from_cells(const Args<P>& a, int i, typen
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_set_state(Args<P> a) {
     using real = typename P::real;
-    using pos4 = typename P::pos4;
     int64_t i = gtid();
     if (i >= a.n) return;
     int c[3];
@@ -322,13 +439,19 @@ __global__ void __launch_bounds__(kBlock) k_set_state(Args<P> a) {
         bad |= !isfinite(v);
     }
     if (bad) atomicOr(&a.ctr->error, kErrUnstable);
-    a.cell[i] = (c[2] * a.G[1] + c[1]) * a.G[0] + c[0];
+    a.cell[i] = pack_cell(c[0], c[1], c[2]);
     a.perm[i] = (int)i;
     a.pbx[i] = pb[0]; a.pby[i] = pb[1]; a.pbz[i] = pb[2];
     a.ox[i] = o[0]; a.oy[i] = o[1]; a.oz[i] = o[2];
-    a.vx[i] = (typename P::vel)a.io_vel[3 * i + 0];
-    a.vy[i] = (typename P::vel)a.io_vel[3 * i + 1];
-    a.vz[i] = (typename P::vel)a.io_vel[3 * i + 2];
+    if constexpr (P::kFp64) {
+        a.vx[i] = a.io_vel[3 * i + 0];
+        a.vy[i] = a.io_vel[3 * i + 1];
+        a.vz[i] = a.io_vel[3 * i + 2];
+    } else {
+        a.vx[i] = cvt::f32(a.io_vel[3 * i + 0]);
+        a.vy[i] = cvt::f32(a.io_vel[3 * i + 1]);
+        a.vz[i] = cvt::f32(a.io_vel[3 * i + 2]);
+    }
     a.pA[i] = make_pos4(pair_coord(pb[0], o[0]), pair_coord(pb[1], o[1]), pair_coord(pb[2], o[2]), 0);
 }
 
@@ -357,19 +480,20 @@ __global__ void k_clear_overflow(Counters* C) {
 // rebuild: binning (counting sort), reorder, neighbour list
 // ---------------------------------------------------------------------------
 
-// Moves each atom whose FP64 offset left its cell into the adjacent cell
-// (periodic wrap is an integer operation on the cell coordinate), re-splits
-// the offset, refreshes the pair coordinate and counts the cell's atoms.
+// Re-anchors every atom at its current position: the FP64 offset pb + o
+// becomes the new build offset (o restarts from the rounding remainder); an
+// atom whose offset left its cell moves to the adjacent cell (periodic wrap
+// is an integer operation on the cell coordinate).  Refreshes the pair
+// coordinate and counts the atoms of each cell.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_bin(Args<P> a, int guard) {
     using real = typename P::real;
-    using pos4 = typename P::pos4;
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     int64_t i = gtid();
     if (i >= a.n) return;
     int cc[3];
-    decode_cell(a.cell[i], a.G, cc[0], cc[1], cc[2]);
+    unpack_cell(a.cell[i], cc[0], cc[1], cc[2]);
     real* pbp[3] = {a.pbx, a.pby, a.pbz};
     double* op[3] = {a.ox, a.oy, a.oz};
     real pb[3];
@@ -377,22 +501,25 @@ __global__ void __launch_bounds__(kBlock) k_bin(Args<P> a, int guard) {
     bool bad = false;
     for (int d = 0; d < 3; d++) {
         double t = full_offset(pbp[d][i], op[d][i]);
-        for (int it = 0; it < 2; it++) {
-            if (t >= a.hw[d]) { t = __dsub_rn(t, a.w[d]); cc[d] = wrap_add(cc[d], 1, a.G[d]); }
-            else if (t < -a.hw[d]) { t = __dadd_rn(t, a.w[d]); cc[d] = wrap_add(cc[d], -1, a.G[d]); }
-        }
-        bad |= !(t >= -a.hw[d] && t < a.hw[d]);  // also catches NaN
-        if (!(t >= -a.hw[d] && t < a.hw[d])) t = 0.0;
         split_offset(t, pb[d], o[d]);
+        // an offset clearly inside the cell needs no FP64 comparison
+        if (!(fabsf(to_f32(pb[d])) < a.hwf_in[d])) {
+            for (int it = 0; it < 2; it++) {
+                if (t >= a.hw[d]) { t = __dsub_rn(t, a.w[d]); cc[d] = wrap_add(cc[d], 1, a.G[d]); }
+                else if (t < -a.hw[d]) { t = __dadd_rn(t, a.w[d]); cc[d] = wrap_add(cc[d], -1, a.G[d]); }
+            }
+            bad |= !(t >= -a.hw[d] && t < a.hw[d]);  // also catches NaN
+            if (!(t >= -a.hw[d] && t < a.hw[d])) t = 0.0;
+            split_offset(t, pb[d], o[d]);
+        }
         pbp[d][i] = pb[d];
         op[d][i] = o[d];
     }
     if (bad) atomicOr(&C->error, kErrUnstable);
-    int c = (cc[2] * a.G[1] + cc[1]) * a.G[0] + cc[0];
-    a.cell[i] = c;
-    pos4* pc = C->parity ? a.pB : a.pA;
+    a.cell[i] = pack_cell(cc[0], cc[1], cc[2]);
+    typename P::pos4* pc = C->parity ? a.pB : a.pA;
     pc[i] = make_pos4(pair_coord(pb[0], o[0]), pair_coord(pb[1], o[1]), pair_coord(pb[2], o[2]), 0);
-    a.rank[i] = atomicAdd(&a.count[c], 1);
+    a.rank[i] = atomicAdd(&a.count[linear_cell(cc[0], cc[1], cc[2], a.G)], 1);
 }
 
 // Exclusive scan of the cell counts, phase 1: per-tile totals.
@@ -497,13 +624,10 @@ __global__ void __launch_bounds__(kBlock) k_scan_apply(Args<P> a, int guard) {
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_scatter(Args<P> a, int guard) {
     if (guard && !a.ctr->rebuild_flag) return;
-    int64_t lim = a.n > a.ncells ? a.n : a.ncells;
-    for (int64_t t = gtid(); t < lim; t += (int64_t)gridDim.x * blockDim.x) {
-        if (t < a.n) {
-            int slot = a.cell_start[a.cell[t]] + a.rank[t];
-            if (slot >= 0 && slot < a.n) a.order[slot] = (int)t;
-            else atomicOr(&a.ctr->error, kErrUnstable);
-        }
+    for (int64_t t = gtid(); t < a.n; t += (int64_t)gridDim.x * blockDim.x) {
+        int slot = a.cell_start[linear_of_packed(a.cell[t], a.G)] + a.rank[t];
+        if (slot >= 0 && slot < a.n) a.order[slot] = (int)t;
+        else atomicOr(&a.ctr->error, kErrUnstable);
     }
     // counts are no longer needed once cell_start is known
     for (int64_t t = gtid(); t < a.ncells; t += (int64_t)gridDim.x * blockDim.x) a.count[t] = 0;
@@ -527,12 +651,11 @@ __global__ void __launch_bounds__(kBlock) k_cellsort(Args<P> a, int guard) {
     }
 }
 
-// Writes the cell-ordered coordinate copy used by the neighbour search and,
-// when a reorder is due, the state permuted into cell order (Sec. 2.5).
+// Writes the cell-ordered FP32 coordinate copy used by the neighbour search
+// and, when a reorder is due, the state permuted into cell order (Sec. 3.5).
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_gather(Args<P> a, int guard) {
     using real = typename P::real;
-    using pos4 = typename P::pos4;
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     int64_t s = gtid();
@@ -542,7 +665,7 @@ __global__ void __launch_bounds__(kBlock) k_gather(Args<P> a, int guard) {
     real pbx = a.pbx[i], pby = a.pby[i], pbz = a.pbz[i];
     double ox = a.ox[i], oy = a.oy[i], oz = a.oz[i];
     real px = pair_coord(pbx, ox), py = pair_coord(pby, oy), pz = pair_coord(pbz, oz);
-    a.cand[s] = make_pos4(px, py, pz, reorder ? (int)s : i);
+    a.cand[s] = make_float4(to_f32(px), to_f32(py), to_f32(pz), __int_as_float(reorder ? (int)s : i));
     if (reorder) {
         a.s_cell[s] = a.cell[i];
         a.s_perm[s] = a.perm[i];
@@ -552,10 +675,10 @@ __global__ void __launch_bounds__(kBlock) k_gather(Args<P> a, int guard) {
     }
 }
 
-// Copies the permuted state back (only when a reorder is due).
+// Copies the permuted state back and rewrites the current pair buffer in
+// the new order (only when a reorder is due).
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
-    using pos4 = typename P::pos4;
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     if (!C->reorder_now) return;
@@ -563,12 +686,13 @@ __global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
     if (s >= a.n) return;
     a.cell[s] = a.s_cell[s];
     a.perm[s] = a.s_perm[s];
-    a.pbx[s] = a.s_pbx[s]; a.pby[s] = a.s_pby[s]; a.pbz[s] = a.s_pbz[s];
-    a.ox[s] = a.s_ox[s]; a.oy[s] = a.s_oy[s]; a.oz[s] = a.s_oz[s];
+    auto pbx = a.s_pbx[s], pby = a.s_pby[s], pbz = a.s_pbz[s];
+    double ox = a.s_ox[s], oy = a.s_oy[s], oz = a.s_oz[s];
+    a.pbx[s] = pbx; a.pby[s] = pby; a.pbz[s] = pbz;
+    a.ox[s] = ox; a.oy[s] = oy; a.oz[s] = oz;
     a.vx[s] = a.s_vx[s]; a.vy[s] = a.s_vy[s]; a.vz[s] = a.s_vz[s];
-    pos4 p = a.cand[s];
-    pos4* pc = C->parity ? a.pB : a.pA;
-    pc[s] = p;
+    typename P::pos4* pc = C->parity ? a.pB : a.pA;
+    pc[s] = make_pos4(pair_coord(pbx, ox), pair_coord(pby, oy), pair_coord(pbz, oz), 0);
 }
 
 // Exact FP64 neighbour criterion r^2 < r_n^2 on the cell-relative offsets
@@ -585,15 +709,14 @@ __device__ __forceinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, i
     return r2 < a.rn2;
 }
 
-// Neighbour-list build (Sec. 2.4): for the atom in cell-ordered slot s, scan
-// the 27 cells around its cell and record every j != i with r < r_n in its
-// column together with the cell-offset code.  The decision is the FP64
-// criterion; the mixed form evaluates it only for candidates whose FP32
-// distance falls in a narrow band around r_n.
+// Neighbour-list build (Sec. 3.4): for the atom in cell-ordered slot s, scan
+// the 27 cells around its cell -- as 9 rows of 3 cells, contiguous in cell
+// order unless the row wraps -- and record every j != i with r < r_n in its
+// column together with the cell-offset code.  The decision is the exact
+// FP64 criterion; FP32 coordinates settle every candidate outside a narrow
+// band around r_n^2 and the FP64 test the rest.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
-    using real = typename P::real;
-    using pos4 = typename P::pos4;
     __shared__ int shm[kBlock / 32];
     __shared__ double shs[kBlock / 32];
     Counters* C = a.ctr;
@@ -601,53 +724,60 @@ __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
     int64_t s = gtid();
     int m = 0;
     if (s < a.n) {
-        pos4 ci = a.cand[s];
-        int i = pos4_index(ci);
+        float4 ci = a.cand[s];
+        int i = __float_as_int(ci.w);
         int cx, cy, cz;
-        decode_cell(a.cell[i], a.G, cx, cy, cz);
+        unpack_cell(a.cell[i], cx, cy, cz);
         int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
+        const float qxm = ci.x + a.wf[0], qxp = ci.x - a.wf[0];  // x seen from cells x-1 and x+1
+        const bool inner = cx >= 1 && cx <= a.G[0] - 2;
+        const int xm = wrap_add(cx, -1, a.G[0]), xp = wrap_add(cx, 1, a.G[0]);
         for (int dz = -1; dz <= 1; dz++) {
             int z = wrap_add(cz, dz, a.G[2]);
+            float qz = ci.z - (float)dz * a.wf[2];
             for (int dy = -1; dy <= 1; dy++) {
                 int y = wrap_add(cy, dy, a.G[1]);
-                for (int dx = -1; dx <= 1; dx++) {
-                    int x = wrap_add(cx, dx, a.G[0]);
-                    int c2 = (z * a.G[1] + y) * a.G[0] + x;
-                    unsigned code = (unsigned)(dx + 1) | ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
-                    int beg = a.cell_start[c2], end = min(a.cell_start[c2 + 1], (int)a.n);
-                    if constexpr (P::kFp64) {
-                        double sx = __dmul_rn(-(double)dx, a.w[0]);
-                        double sy = __dmul_rn(-(double)dy, a.w[1]);
-                        double sz = __dmul_rn(-(double)dz, a.w[2]);
-                        for (int t = beg; t < end; t++) {
-                            if (t == s) continue;
-                            pos4 pj = ld_pos4(a.cand + t);
-                            double ex = __dadd_rn(__dsub_rn((double)ci.x, (double)pj.x), sx);
-                            double ey = __dadd_rn(__dsub_rn((double)ci.y, (double)pj.y), sy);
-                            double ez = __dadd_rn(__dsub_rn((double)ci.z, (double)pj.z), sz);
-                            double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-                            if (r2 < a.rn2) {
-                                if (m < a.cap) col[(size_t)m * 32] = pos4_index(pj) | (int)(code << kCodeShift);
-                                m++;
-                            }
-                        }
-                    } else {
-                        float sx = -(float)dx * a.wf[0];
-                        float sy = -(float)dy * a.wf[1];
-                        float sz = -(float)dz * a.wf[2];
-                        for (int t = beg; t < end; t++) {
-                            if (t == s) continue;
-                            pos4 pj = ld_pos4(a.cand + t);
-                            float ex = ((float)ci.x - (float)pj.x) + sx;
-                            float ey = ((float)ci.y - (float)pj.y) + sy;
-                            float ez = ((float)ci.z - (float)pj.z) + sz;
-                            float r2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                            bool take = r2 < a.rn2_lo;
-                            if (!take && r2 < a.rn2_hi) take = within_rn_fp64(a, i, pos4_index(pj), dx, dy, dz);
-                            if (take) {
-                                if (m < a.cap) col[(size_t)m * 32] = pos4_index(pj) | (int)(code << kCodeShift);
-                                m++;
-                            }
+                float qy = ci.y - (float)dy * a.wf[1];
+                unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
+                int row = (z * a.G[1] + y) * a.G[0];
+                // cells x-1, x, x+1 of this row: [r0, r1), [r1, r2), [r2, r3)
+                // when contiguous, else three separate ranges
+                int r0, r1, r2, r3, e0, f0;
+                if (inner) {
+                    r0 = a.cell_start[row + cx - 1];
+                    r1 = a.cell_start[row + cx];
+                    r2 = a.cell_start[row + cx + 1];
+                    r3 = a.cell_start[row + cx + 2];
+                    e0 = r1;
+                    f0 = r2;
+                } else {
+                    r0 = a.cell_start[row + xm];
+                    e0 = a.cell_start[row + xm + 1];
+                    r1 = a.cell_start[row + cx];
+                    r2 = a.cell_start[row + cx + 1];
+                    f0 = a.cell_start[row + xp];
+                    r3 = a.cell_start[row + xp + 1];
+                }
+                // pieces: [r0, e0) is x-1, [r1, r2) is x, [f0, r3) is x+1
+                for (int piece = 0; piece < 3; piece++) {
+                    int lo = piece == 0 ? r0 : (piece == 1 ? r1 : f0);
+                    int hi = piece == 0 ? e0 : (piece == 1 ? r2 : r3);
+                    hi = min(hi, (int)a.n);
+                    const float qx = piece == 0 ? qxm : (piece == 1 ? ci.x : qxp);
+                    const unsigned code = (unsigned)piece | code_yz;
+                    for (int t = lo; t < hi; t++) {
+                        if (t == s) continue;
+                        float4 pj = __ldg(a.cand + t);
+                        float ex = qx - pj.x;
+                        float ey = qy - pj.y;
+                        float ez = qz - pj.z;
+                        float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        int j = __float_as_int(pj.w);
+                        bool take = rr < a.rn2_lo;
+                        if (!take && rr < a.rn2_hi) take = within_rn_fp64(a, i, j, piece - 1, dy, dz);
+                        if (take) {
+                            if (m < a.cap) col[(size_t)m * 32] = j | (int)(code << kCodeShift);
+                            m++;
                         }
                     }
                 }
@@ -695,7 +825,7 @@ __global__ void k_cond(Args<P> a, cudaGraphConditionalHandle h) {
 
 // Rebuild decision at the end of a drift: list invalid once some atom has
 // moved skin/2 (every step in the cell-list-only variant); reorder when
-// reorder_interval steps have passed (Sec. 5.4).
+// reorder_interval steps have passed (Sec. 5.5).
 __device__ __forceinline__ int decide_rebuild(Counters* C, int cell_list_only, int interval) {
     int need = (C->far_flag != 0u) || cell_list_only;
     C->far_flag = 0u;
@@ -704,7 +834,11 @@ __device__ __forceinline__ int decide_rebuild(Counters* C, int cell_list_only, i
     return need;
 }
 
-// First half of the first step of an md_step call (Sec. 2.1 (a)): half kick
+// Half kick in the velocity precision.
+__device__ __forceinline__ float kick(const Args<Mixed>& a, float v, float f) { return fmaf(a.hf, f, v); }
+__device__ __forceinline__ double kick(const Args<F64>& a, double v, double f) { return fma(a.h, f, v); }
+
+// First half of the first step of an md_step call (Sec. 3.1 (a)): half kick
 // with the stored forces, drift, displacement test.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_kickdrift(Args<P> a, long long nsteps) {
@@ -719,29 +853,19 @@ __global__ void __launch_bounds__(kBlock) k_kickdrift(Args<P> a, long long nstep
     bool far = false;
     if (!err && i < a.n) {
         pos4* pc = par ? a.pB : a.pA;
-        vel vx = a.vx[i], vy = a.vy[i], vz = a.vz[i];
-        double ox = a.ox[i], oy = a.oy[i], oz = a.oz[i];
-        if constexpr (P::kFp64) {
-            vx = fma((double)a.h, (double)a.fx[i], (double)vx);
-            vy = fma((double)a.h, (double)a.fy[i], (double)vy);
-            vz = fma((double)a.h, (double)a.fz[i], (double)vz);
-        } else {
-            vx = fmaf(a.hf, (float)a.fx[i], (float)vx);
-            vy = fmaf(a.hf, (float)a.fy[i], (float)vy);
-            vz = fmaf(a.hf, (float)a.fz[i], (float)vz);
-        }
-        ox = fma((double)vx, a.dt, ox);
-        oy = fma((double)vy, a.dt, oy);
-        oz = fma((double)vz, a.dt, oz);
-        real px = pair_coord(a.pbx[i], ox), py = pair_coord(a.pby[i], oy), pz = pair_coord(a.pbz[i], oz);
+        vel vx = kick(a, a.vx[i], a.fx[i]);
+        vel vy = kick(a, a.vy[i], a.fy[i]);
+        vel vz = kick(a, a.vz[i], a.fz[i]);
+        double ox = drift(a.ox[i], vx, a.dt);
+        double oy = drift(a.oy[i], vy, a.dt);
+        double oz = drift(a.oz[i], vz, a.dt);
+        real px, py, pz;
+        real d2 = moved(a.pbx[i], ox, px) + moved(a.pby[i], oy, py) + moved(a.pbz[i], oz, pz);
         a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
         a.ox[i] = ox; a.oy[i] = oy; a.oz[i] = oz;
         pc[i] = make_pos4(px, py, pz, 0);
-        if constexpr (P::kFp64) far = ox * ox + oy * oy + oz * oz >= a.thr2;
-        else {
-            float fx = __double2float_rn(ox), fy = __double2float_rn(oy), fz = __double2float_rn(oz);
-            far = fmaf(fx, fx, fmaf(fy, fy, fz * fz)) >= a.thr2f;
-        }
+        if constexpr (P::kFp64) far = d2 >= a.thr2;
+        else far = d2 >= a.thr2f;
     }
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
     if (last_block_done(C)) {
@@ -755,14 +879,15 @@ __global__ void __launch_bounds__(kBlock) k_kickdrift(Args<P> a, long long nstep
     }
 }
 
-// Force + integration kernel (Sec. 2.1 (c)-(e) of one step and (a) of the
-// next).  Mode kModeInit computes the forces of a freshly loaded state.
-// Mode kModeAuto completes a step: forces f_n, v_n = v_{n-1/2} + f_n dt/2;
-// then, unless it is the last step of the call, v_{n+1/2} = v_n + f_n dt/2,
-// o += v_{n+1/2} dt into the other pair-coordinate buffer and the skin/2
-// test.  The last block advances the counters and, in a graph, sets the
-// next conditional rebuild node.
-template <class P, bool kCells>
+// Force + integration kernel (Sec. 3.1 (c)-(e) of one step and (a) of the
+// next).  A full step: forces f_n, v_n = v_{n-1/2} + f_n dt/2,
+// v_{n+1/2} = v_n + f_n dt/2, o += v_{n+1/2} dt into the other pair buffer
+// and the skin/2 test.  The kFinal variant also handles the last step of an
+// md_step call (forces, v_n, PE/W/KE partials, no drift) and mode
+// kModeInit (forces of a freshly loaded state); the plain variant, used for
+// every other step, carries no energy accumulators.  The last block
+// advances the counters and, in a graph, sets the next conditional rebuild.
+template <class P, bool kCells, bool kFinal>
 __global__ void __launch_bounds__(kBlock) k_step(Args<P> a, int mode, cudaGraphConditionalHandle next,
                                                  int has_next) {
     using real = typename P::real;
@@ -774,9 +899,10 @@ __global__ void __launch_bounds__(kBlock) k_step(Args<P> a, int mode, cudaGraphC
     const int err = vw.err;
     const long long left = vw.left;
     const int par = vw.par;
-    const bool init = (mode == kModeInit);
-    const bool active = init || (err == 0 && left > 0);
-    const bool last = !init && left == 1;
+    const bool init = kFinal && (mode == kModeInit);
+    const bool last = kFinal && !init && left == 1;
+    const bool misplaced = !kFinal && left == 1;  // a plain node must never run a call's last step
+    const bool active = init || (err == 0 && left > 0 && !misplaced);
     const bool energy = init || last;
     const pos4* pc = par ? a.pB : a.pA;
     pos4* pn = par ? a.pA : a.pB;
@@ -788,68 +914,65 @@ __global__ void __launch_bounds__(kBlock) k_step(Args<P> a, int mode, cudaGraphC
         double ox = a.ox[i], oy = a.oy[i], oz = a.oz[i];
         real qx = pair_coord(pbx, ox), qy = pair_coord(pby, oy), qz = pair_coord(pbz, oz);
         typename AccOf<P>::type acc;
-        if (kCells) forces_from_cells<P>(a, (int)i, qx, qy, qz, energy, acc);
-        else forces_from_list<P>(a, (int)i, qx, qy, qz, pc, energy, acc);
+        if (kFinal && energy) {
+            if constexpr (kCells) forces_from_cells<P, kFinal>(a, (int)i, qx, qy, qz, pc, acc);
+            else forces_from_list<P, kFinal>(a, (int)i, qx, qy, qz, pc, acc);
+        } else {
+            if constexpr (kCells) forces_from_cells<P, false>(a, (int)i, qx, qy, qz, pc, acc);
+            else forces_from_list<P, false>(a, (int)i, qx, qy, qz, pc, acc);
+        }
         close = acc.close != 0;
         real fx = acc.force_x(), fy = acc.force_y(), fz = acc.force_z();
         vel vx = a.vx[i], vy = a.vy[i], vz = a.vz[i];
         if (!init) {
-            if constexpr (P::kFp64) {
-                vx = fma((double)a.h, (double)fx, (double)vx);
-                vy = fma((double)a.h, (double)fy, (double)vy);
-                vz = fma((double)a.h, (double)fz, (double)vz);
-            } else {
-                vx = fmaf(a.hf, (float)fx, (float)vx);
-                vy = fmaf(a.hf, (float)fy, (float)vy);
-                vz = fmaf(a.hf, (float)fz, (float)vz);
-            }
+            vx = kick(a, vx, fx);
+            vy = kick(a, vy, fy);
+            vz = kick(a, vz, fz);
         }
         if (energy) {
             a.fx[i] = fx; a.fy[i] = fy; a.fz[i] = fz;
-            double dvx = vx, dvy = vy, dvz = vz;
+            double dvx, dvy, dvz;
+            if constexpr (P::kFp64) { dvx = vx; dvy = vy; dvz = vz; }
+            else { dvx = cvt::f64(vx); dvy = cvt::f64(vy); dvz = cvt::f64(vz); }
             ke = 0.5 * (dvx * dvx + dvy * dvy + dvz * dvz);
             pe = 0.5 * acc.energy();
             vir = 0.5 * acc.virial();
             if (!init) { a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz; }
         } else {
-            if constexpr (P::kFp64) {
-                vx = fma((double)a.h, (double)fx, (double)vx);
-                vy = fma((double)a.h, (double)fy, (double)vy);
-                vz = fma((double)a.h, (double)fz, (double)vz);
-            } else {
-                vx = fmaf(a.hf, (float)fx, (float)vx);
-                vy = fmaf(a.hf, (float)fy, (float)vy);
-                vz = fmaf(a.hf, (float)fz, (float)vz);
-            }
-            ox = fma((double)vx, a.dt, ox);
-            oy = fma((double)vy, a.dt, oy);
-            oz = fma((double)vz, a.dt, oz);
+            vx = kick(a, vx, fx);
+            vy = kick(a, vy, fy);
+            vz = kick(a, vz, fz);
+            ox = drift(ox, vx, a.dt);
+            oy = drift(oy, vy, a.dt);
+            oz = drift(oz, vz, a.dt);
+            real px, py, pz;
+            real d2 = moved(pbx, ox, px) + moved(pby, oy, py) + moved(pbz, oz, pz);
             a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
             a.ox[i] = ox; a.oy[i] = oy; a.oz[i] = oz;
-            pn[i] = make_pos4(pair_coord(pbx, ox), pair_coord(pby, oy), pair_coord(pbz, oz), 0);
-            if constexpr (P::kFp64) far = ox * ox + oy * oy + oz * oz >= a.thr2;
-            else {
-                float dx = __double2float_rn(ox), dy = __double2float_rn(oy), dz = __double2float_rn(oz);
-                far = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) >= a.thr2f;
-            }
+            pn[i] = make_pos4(px, py, pz, 0);
+            if constexpr (P::kFp64) far = d2 >= a.thr2;
+            else far = d2 >= a.thr2f;
         }
     }
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
     if (__any_sync(0xffffffffu, close) && (threadIdx.x & 31) == 0) atomicOr(&C->close_flag, 1);
-    if (energy && active) {
-        double bk = block_sum(ke, shs);
-        double bp = block_sum(pe, shs);
-        double bw = block_sum(vir, shs);
-        if (threadIdx.x == 0) {
-            a.part[3 * blockIdx.x + 0] = bk;
-            a.part[3 * blockIdx.x + 1] = bp;
-            a.part[3 * blockIdx.x + 2] = bw;
+    if constexpr (kFinal) {
+        if (energy && active) {
+            double bk = block_sum(ke, shs);
+            double bp = block_sum(pe, shs);
+            double bw = block_sum(vir, shs);
+            if (threadIdx.x == 0) {
+                a.part[3 * blockIdx.x + 0] = bk;
+                a.part[3 * blockIdx.x + 1] = bp;
+                a.part[3 * blockIdx.x + 2] = bw;
+            }
         }
     }
     if (last_block_done(C)) {
         if (threadIdx.x == 0) {
             int need = 0;
-            if (!init && err == 0 && left > 0) {
+            if (misplaced && err == 0) C->error |= kErrInternal;
+            if (active && !init) {
                 C->steps_left = left - 1;
                 C->step += 1;
                 C->since_reorder += 1;
@@ -900,7 +1023,7 @@ __global__ void __launch_bounds__(kBlock) k_get_state(Args<P> a) {
     if (i >= a.n) return;
     int u = a.perm[i];
     int cc[3];
-    decode_cell(a.cell[i], a.G, cc[0], cc[1], cc[2]);
+    unpack_cell(a.cell[i], cc[0], cc[1], cc[2]);
     const typename P::real* pb[3] = {a.pbx, a.pby, a.pbz};
     const double* o[3] = {a.ox, a.oy, a.oz};
     const typename P::vel* v[3] = {a.vx, a.vy, a.vz};
@@ -910,7 +1033,8 @@ __global__ void __launch_bounds__(kBlock) k_get_state(Args<P> a) {
         double s = floor(__dmul_rn(__dadd_rn(x, a.hL[d]), a.invL[d]));
         x = __dsub_rn(x, __dmul_rn(s, a.L[d]));
         a.io_pos[3 * (int64_t)u + d] = x;
-        a.io_vel[3 * (int64_t)u + d] = (double)v[d][i];
+        if constexpr (P::kFp64) a.io_vel[3 * (int64_t)u + d] = v[d][i];
+        else a.io_vel[3 * (int64_t)u + d] = cvt::f64(v[d][i]);
     }
 }
 
@@ -919,16 +1043,58 @@ __global__ void __launch_bounds__(kBlock) k_get_forces(Args<P> a, double* out) {
     int64_t i = gtid();
     if (i >= a.n) return;
     int64_t u = a.perm[i];
-    out[3 * u + 0] = (double)a.fx[i];
-    out[3 * u + 1] = (double)a.fy[i];
-    out[3 * u + 2] = (double)a.fz[i];
+    if constexpr (P::kFp64) {
+        out[3 * u + 0] = a.fx[i];
+        out[3 * u + 1] = a.fy[i];
+        out[3 * u + 2] = a.fz[i];
+    } else {
+        out[3 * u + 0] = cvt::f64(a.fx[i]);
+        out[3 * u + 1] = cvt::f64(a.fy[i]);
+        out[3 * u + 2] = cvt::f64(a.fz[i]);
+    }
 }
 
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_get_cells(Args<P> a, int* out) {
     int64_t i = gtid();
     if (i >= a.n) return;
-    out[a.perm[i]] = a.cell[i];
+    out[a.perm[i]] = linear_of_packed(a.cell[i], a.G);
+}
+
+// Compares the FP32/integer-pipe conversions with the hardware conversions
+// on hashed bit patterns spanning the magnitudes the step uses.  fails[k]
+// counts mismatches of f64, f32, the fixed-point accumulation and from_fix.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_selftest(long long n, unsigned long long* fails) {
+    long long t = gtid();
+    if (t >= n) return;
+    unsigned long long r = mix64((unsigned long long)t);
+    unsigned long long r2 = mix64(r);
+    // binary32 with exponent in [2^-100, 2^60), random sign and mantissa
+    unsigned e32 = 27u + (unsigned)(r % 160u);
+    float x = __uint_as_float((unsigned)((r >> 8) & 0x807FFFFFu) | (e32 << 23));
+    if (__double_as_longlong(cvt::f64(x)) != __double_as_longlong((double)x)) atomicAdd(&fails[0], 1ull);
+    // binary64 inside the binary32 normal range
+    unsigned long long e64 = 1023ull - 120ull + (r2 % 240ull);
+    double d = __longlong_as_double((long long)((r2 & 0x800FFFFFFFFFFFFFull) | (e64 << 52)));
+    if (__float_as_uint(cvt::f32(d)) != __float_as_uint(__double2float_rn(d))) atomicAdd(&fails[1], 1ull);
+    // fixed point: g with |g| in [2^-40, 2^30); g and -g cancel exactly
+    float g = __uint_as_float((unsigned)((r >> 16) & 0x807FFFFFu) | ((87u + (unsigned)(r2 % 70u)) << 23));
+    Fix one, both;
+    one.add(g);
+    both.add(g);
+    both.add(-g);
+    long long ref = __float2ll_rn(g * 4294967296.0f);  // the product is exact
+    if (one.value() != ref || both.value() != 0) atomicAdd(&fails[2], 1ull);
+    long long qq = (long long)(r2 >> (r % 64u)) * ((r & 1u) ? -1 : 1);
+    if (__float_as_uint(cvt::from_fix(qq)) != __float_as_uint(__ll2float_rn(qq))) atomicAdd(&fails[3], 1ull);
 }
 
 // ---------------------------------------------------------------------------
@@ -951,14 +1117,17 @@ KernelTable<P> make_kernel_table() {
     t.rebuild_done = (void*)k_rebuild_done<P>;
     t.cond = (void*)k_cond<P>;
     t.kickdrift = (void*)k_kickdrift<P>;
-    t.step_list = (void*)k_step<P, false>;
-    t.step_cells = (void*)k_step<P, true>;
+    t.step_list = (void*)k_step<P, false, false>;
+    t.step_list_final = (void*)k_step<P, false, true>;
+    t.step_cells = (void*)k_step<P, true, false>;
+    t.step_cells_final = (void*)k_step<P, true, true>;
     t.finalize = (void*)k_finalize<P>;
     t.get_state = (void*)k_get_state<P>;
     t.get_forces = (void*)k_get_forces<P>;
     t.get_cells = (void*)k_get_cells<P>;
     t.reset_counters = (void*)k_reset_counters<P>;
     t.clear_overflow = (void*)k_clear_overflow<P>;
+    t.selftest = (void*)k_selftest<P>;
     return t;
 }
 

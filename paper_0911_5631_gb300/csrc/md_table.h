@@ -21,13 +21,16 @@ struct KernelTable {
     void* cond;
     void* kickdrift;
     void* step_list;
+    void* step_list_final;
     void* step_cells;
+    void* step_cells_final;
     void* finalize;
     void* get_state;
     void* get_forces;
     void* get_cells;
     void* reset_counters;
     void* clear_overflow;
+    void* selftest;
 };
 
 template <class P>

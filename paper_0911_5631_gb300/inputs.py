@@ -9,7 +9,7 @@ pseudorandom number generators", OOPSLA 2014): state += 0x9E3779B97F4A7C15,
 then the xor-shift-multiply finaliser.  Uniform doubles take the top 53
 bits; normal deviates use the Box-Muller transform.
 
-Initial states follow the paper's recipe (Sec. 2.5: lattice start, velocity
+Initial states follow the paper's recipe (Sec. 3.5: lattice start, velocity
 of given temperature, centre of mass at rest) with an FCC lattice and
 Maxwell-distributed velocities in place of the simple cubic lattice and
 fixed speed.

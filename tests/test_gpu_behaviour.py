@@ -16,7 +16,7 @@ def _built():
 
 
 def _run(prec, steps=300, n=4000, seed=7, **kw):
-    pos, vel, L = state(n, 0.8, 1.5, seed, jitter=0.15)
+    pos, vel, L = state(n, 0.8, 1.5, seed, jitter=0.05)
     s = sim(pos, vel, L, skin=0.4, precision=prec, **kw)
     s.step(steps)
     p, v = s.get_state()
@@ -69,8 +69,14 @@ def test_capacity_growth_is_transparent(prec):
         assert np.array_equal(x, y)
 
 
+def test_integer_conversions_match_hardware():
+    # the mixed form converts on the integer pipe; check every routine
+    # against the hardware conversion on 2^24 hashed inputs
+    assert md.md_selftest(1 << 24) == [0, 0, 0, 0]
+
+
 def test_step_chunking_is_transparent():
-    pos, vel, L = state(2048, 0.8, 1.0, 3, jitter=0.1)
+    pos, vel, L = state(2048, 0.8, 1.0, 3, jitter=0.05)
     s1 = sim(pos, vel, L)
     s1.step(100)
     s2 = sim(pos, vel, L)
@@ -109,12 +115,13 @@ def test_errors_are_reported():
 
 def test_state_round_trip_and_device_pointers():
     torch = pytest.importorskip("torch")
-    pos, vel, L = state(1372, 0.8, 1.0, 9, jitter=0.1)
+    pos, vel, L = state(1372, 0.8, 1.0, 9, jitter=0.05)
     s = sim(pos, vel, L)
     p, v = s.get_state()
     pw = oracle.wrap(pos, L)
     assert np.abs(p - pw).max() < 1e-13
-    assert np.abs(v - vel).max() < 1e-7  # FP32 velocity storage
+    # FP32 velocity storage: round to nearest, relative error <= 2^-24
+    assert np.all(np.abs(v - vel) <= 2.0 ** -24 * np.abs(vel))
     tp = torch.tensor(pos, device="cuda")
     tv = torch.tensor(vel, device="cuda")
     s.set_state(tp, tv)

@@ -16,7 +16,7 @@ RC = 2.0 ** (1.0 / 6.0)
 
 
 # --------------------------------------------------------------------------
-# Pair term, Eq. (1) + soft-sphere shift (Sec. 2.1)
+# Pair term, Eq. (1) + soft-sphere shift (Sec. 3.1)
 # --------------------------------------------------------------------------
 
 def test_pair_closed_forms():
@@ -77,7 +77,7 @@ def test_three_collinear_atoms():
 
 
 # --------------------------------------------------------------------------
-# Region, wrap and cells (Sec. 2.1, 2.2, 4.2)
+# Region, wrap and cells (Sec. 3.1, 3.2, 4.2)
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("row", read_golden("paper_cell_counts.txt"))
@@ -119,7 +119,7 @@ def test_cell_of_known_cells():
 
 
 # --------------------------------------------------------------------------
-# Pair enumeration: half-shell cell lists == O(N^2) definition (Sec. 2.2)
+# Pair enumeration: half-shell cell lists == O(N^2) definition (Sec. 3.2)
 # --------------------------------------------------------------------------
 
 def _as_set(pairs):
@@ -210,12 +210,12 @@ def test_sampled_forces_and_full_list_energy():
     idx = np.arange(500)
     fs, us = oracle.forces_sampled(pos, L, RC, 1.0, idx)
     assert np.allclose(fs, fb, rtol=0, atol=1e-11 * np.abs(fb).max())
-    # the per-atom sums over all partners count each pair twice (Sec. 2.3)
+    # the per-atom sums over all partners count each pair twice (Sec. 3.3)
     assert us.sum() == pytest.approx(2 * Ub, rel=1e-12)
 
 
 # --------------------------------------------------------------------------
-# The MD loop (Sec. 2.1)
+# The MD loop (Sec. 3.1)
 # --------------------------------------------------------------------------
 
 def _fluid(n=500, rho=0.8, T=1.0, seed=21, jit=0.2):
