@@ -263,26 +263,37 @@ __device__ __forceinline__ float to_f32(double x) { return cvt::f32(x); }
 struct AccMixed {
     Fix fx, fy, fz, u, w;
     int close = 0;
+    // accumulate one interacting pair (r^2 < r_c^2) at separation d
     template <bool kEnergy>
-    __device__ __forceinline__ void pair(const Args<Mixed>& a, float dx, float dy, float dz) {
-        float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (r2 < a.rc2f) {
-            close |= (r2 < a.close2f);
-            float ir2 = __frcp_rn(r2);
-            float ir6 = ir2 * ir2 * ir2;
-            float fr = 48.0f * ir6 * (ir6 - 0.5f) * ir2;
-            fx.add(fr * dx);
-            fy.add(fr * dy);
-            fz.add(fr * dz);
-            if constexpr (kEnergy) {
-                u.add(fmaf(4.0f * ir6, ir6 - 1.0f, a.ushiftf));
-                w.add(fr * r2);
-            }
+    __device__ __forceinline__ void force(const Args<Mixed>& a, float dx, float dy, float dz, float r2) {
+        close |= (r2 < a.close2f);
+        float ir2 = __fdividef(1.0f, r2);
+        float ir6 = ir2 * ir2 * ir2;
+        float fr = 48.0f * ir6 * (ir6 - 0.5f) * ir2;
+        fx.add(fr * dx);
+        fy.add(fr * dy);
+        fz.add(fr * dz);
+        if constexpr (kEnergy) {
+            u.add(fmaf(4.0f * ir6, ir6 - 1.0f, a.ushiftf));
+            w.add(fr * r2);
         }
     }
-    __device__ __forceinline__ float force_x() const { return cvt::from_fix(fx.value()) * kFixInvF; }
-    __device__ __forceinline__ float force_y() const { return cvt::from_fix(fy.value()) * kFixInvF; }
-    __device__ __forceinline__ float force_z() const { return cvt::from_fix(fz.value()) * kFixInvF; }
+    __device__ __forceinline__ float r2(float dx, float dy, float dz) const { return fmaf(dx, dx, fmaf(dy, dy, dz * dz)); }
+    __device__ __forceinline__ bool inside(const Args<Mixed>& a, float r2) const { return r2 < a.rc2f; }
+    template <bool kEnergy>
+    __device__ __forceinline__ void pair(const Args<Mixed>& a, float dx, float dy, float dz) {
+        float rr = r2(dx, dy, dz);
+        if (inside(a, rr)) force<kEnergy>(a, dx, dy, dz, rr);
+    }
+    // Per-atom force from the three exact partial sums.  The rounding is
+    // not the correctly rounded one, but it is a fixed function of sums
+    // that do not depend on the order of the pairs.
+    __device__ __forceinline__ static float to_force(const Fix& q) {
+        return fmaf((float)q.a, 4096.0f, fmaf((float)q.b, 0x1p-10f, (float)q.c * 0x1p-32f));
+    }
+    __device__ __forceinline__ float force_x() const { return to_force(fx); }
+    __device__ __forceinline__ float force_y() const { return to_force(fy); }
+    __device__ __forceinline__ float force_z() const { return to_force(fz); }
     __device__ __forceinline__ double energy() const { return (double)u.value() * kFixInv; }
     __device__ __forceinline__ double virial() const { return (double)w.value() * kFixInv; }
 };
@@ -292,21 +303,25 @@ struct AccF64 {
     double fx = 0, fy = 0, fz = 0, u = 0, w = 0;
     int close = 0;
     template <bool kEnergy>
-    __device__ __forceinline__ void pair(const Args<F64>& a, double dx, double dy, double dz) {
-        double r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < a.rc2) {
-            close |= (r2 < a.close2);
-            double ir2 = 1.0 / r2;
-            double ir6 = ir2 * ir2 * ir2;
-            double fr = 48.0 * ir6 * (ir6 - 0.5) * ir2;
-            fx += fr * dx;
-            fy += fr * dy;
-            fz += fr * dz;
-            if constexpr (kEnergy) {
-                u += 4.0 * ir6 * (ir6 - 1.0) + a.ushift;
-                w += fr * r2;
-            }
+    __device__ __forceinline__ void force(const Args<F64>& a, double dx, double dy, double dz, double r2) {
+        close |= (r2 < a.close2);
+        double ir2 = 1.0 / r2;
+        double ir6 = ir2 * ir2 * ir2;
+        double fr = 48.0 * ir6 * (ir6 - 0.5) * ir2;
+        fx += fr * dx;
+        fy += fr * dy;
+        fz += fr * dz;
+        if constexpr (kEnergy) {
+            u += 4.0 * ir6 * (ir6 - 1.0) + a.ushift;
+            w += fr * r2;
         }
+    }
+    __device__ __forceinline__ double r2(double dx, double dy, double dz) const { return dx * dx + dy * dy + dz * dz; }
+    __device__ __forceinline__ bool inside(const Args<F64>& a, double r2) const { return r2 < a.rc2; }
+    template <bool kEnergy>
+    __device__ __forceinline__ void pair(const Args<F64>& a, double dx, double dy, double dz) {
+        double rr = r2(dx, dy, dz);
+        if (inside(a, rr)) force<kEnergy>(a, dx, dy, dz, rr);
     }
     __device__ __forceinline__ double force_x() const { return fx; }
     __device__ __forceinline__ double force_y() const { return fy; }
@@ -319,22 +334,58 @@ template <class P> struct AccOf;
 template <> struct AccOf<Mixed> { using type = AccMixed; };
 template <> struct AccOf<F64> { using type = AccF64; };
 
-// Forces on atom i from its neighbour-list column (Sec. 3.4: W_{m,i}, m_i).
-// Entries are read four at a time so several independent loads are in
-// flight per thread.
+// Per-thread queue of interacting pairs (separation, r^2) in shared memory,
+// slot-major so that a warp's accesses are contiguous.
+template <class P> struct Queue;
+template <> struct Queue<Mixed> {
+    using item = float4;
+    static constexpr int kSlots = 10;
+    __device__ __forceinline__ static item make(float x, float y, float z, float r2) { return make_float4(x, y, z, r2); }
+};
+template <> struct Queue<F64> {
+    using item = double4_32a;
+    static constexpr int kSlots = 5;
+    __device__ __forceinline__ static item make(double x, double y, double z, double r2) {
+        return make_double4_32a(x, y, z, r2);
+    }
+};
+
+// Shift -d w for each 6-bit cell-offset code, built per block in shared
+// memory (entries whose code has a component 3 are unused).
+template <class P>
+__device__ __forceinline__ void fill_shift_table(const Args<P>& a, typename P::pos4* tbl) {
+    using real = typename P::real;
+    if (threadIdx.x < 64) {
+        unsigned c = threadIdx.x;
+        real w0, w1, w2;
+        if constexpr (P::kFp64) { w0 = a.w[0]; w1 = a.w[1]; w2 = a.w[2]; }
+        else { w0 = a.wf[0]; w1 = a.wf[1]; w2 = a.wf[2]; }
+        tbl[c] = make_pos4(code_shift<real>(c & 3u, w0), code_shift<real>((c >> 2) & 3u, w1),
+                           code_shift<real>((c >> 4) & 3u, w2), 0);
+    }
+}
+
+// Forces on atom i from its neighbour-list column (Sec. 3.4: W_{m,i}, m_i),
+// in two phases.  Phase 1 reads the entries (four at a time, so several
+// independent loads are in flight), tests r^2 < r_c^2 and queues the
+// interacting separations; phase 2 evaluates the pair term for the queued
+// pairs only.  A warp thus runs the expensive pair term as often as its
+// busiest atom has interacting partners instead of as often as it has
+// neighbour entries.  Pairs beyond the queue are evaluated at once.
 template <class P, bool kEnergy>
 __device__ __forceinline__ void forces_from_list(const Args<P>& a, int i, typename P::real qx,
                                                  typename P::real qy, typename P::real qz,
                                                  const typename P::pos4* __restrict__ pc,
+                                                 const typename P::pos4* __restrict__ shift,
+                                                 typename Queue<P>::item* queue,
                                                  typename AccOf<P>::type& acc) {
     using real = typename P::real;
     using pos4 = typename P::pos4;
+    constexpr int kQ = Queue<P>::kSlots;
     const int cnt = a.nn[i];
     const unsigned nlast = (unsigned)(a.n - 1);  // entries are always < n; the clamp only guards memory
     const int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
-    real wx, wy, wz;
-    if constexpr (P::kFp64) { wx = a.w[0]; wy = a.w[1]; wz = a.w[2]; }
-    else { wx = a.wf[0]; wy = a.wf[1]; wz = a.wf[2]; }
+    int nq = 0;
     for (int m = 0; m < cnt; m += 4) {
         unsigned e[4];
         pos4 pj[4];
@@ -347,13 +398,23 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int i, typena
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (m + k < cnt) {
-                unsigned code = e[k] >> kCodeShift;
-                real dx = (qx - pj[k].x) + code_shift<real>(code & 3u, wx);
-                real dy = (qy - pj[k].y) + code_shift<real>((code >> 2) & 3u, wy);
-                real dz = (qz - pj[k].z) + code_shift<real>((code >> 4) & 3u, wz);
-                acc.template pair<kEnergy>(a, dx, dy, dz);
+                const pos4 sh = shift[e[k] >> kCodeShift];
+                real dx = (qx - pj[k].x) + sh.x;
+                real dy = (qy - pj[k].y) + sh.y;
+                real dz = (qz - pj[k].z) + sh.z;
+                real rr = acc.r2(dx, dy, dz);
+                if (acc.inside(a, rr)) {
+                    if (nq < kQ) queue[nq * kBlock + threadIdx.x] = Queue<P>::make(dx, dy, dz, rr);
+                    else acc.template force<kEnergy>(a, dx, dy, dz, rr);
+                    nq++;
+                }
             }
         }
+    }
+    const int nk = min(nq, kQ);
+    for (int k = 0; k < nk; k++) {
+        const auto d = queue[k * kBlock + threadIdx.x];
+        acc.template force<kEnergy>(a, d.x, d.y, d.z, d.w);
     }
 }
 
@@ -698,7 +759,7 @@ __global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
 // Exact FP64 neighbour criterion r^2 < r_n^2 on the cell-relative offsets
 // (no contraction, fixed operation order).
 template <class P>
-__device__ __forceinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int dx, int dy, int dz) {
+__device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int dx, int dy, int dz) {
     double ex = __dadd_rn(__dsub_rn(full_offset(a.pbx[i], a.ox[i]), full_offset(a.pbx[j], a.ox[j])),
                           __dmul_rn(-(double)dx, a.w[0]));
     double ey = __dadd_rn(__dsub_rn(full_offset(a.pby[i], a.oy[i]), full_offset(a.pby[j], a.oy[j])),
@@ -709,76 +770,84 @@ __device__ __forceinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, i
     return r2 < a.rn2;
 }
 
-// Neighbour-list build (Sec. 3.4): for the atom in cell-ordered slot s, scan
-// the 27 cells around its cell -- as 9 rows of 3 cells, contiguous in cell
-// order unless the row wraps -- and record every j != i with r < r_n in its
-// column together with the cell-offset code.  The decision is the exact
-// FP64 criterion; FP32 coordinates settle every candidate outside a narrow
-// band around r_n^2 and the FP64 test the rest.
+// Neighbour-list build (Sec. 3.4).  One block per row of cells (fixed c_y,
+// c_z; all c_x): the block first stages the cell-ordered FP32 coordinates
+// and the cell starts of the 3 x 3 neighbouring rows in shared memory, then
+// each thread takes one atom of the row and scans the 27 cells around the
+// atom's cell from shared memory, recording every j != i with r < r_n in
+// its column together with the cell-offset code.  The decision is the exact
+// FP64 criterion: FP32 coordinates settle every candidate outside a narrow
+// band around r_n^2, the FP64 test the rest.  A row longer than the staging
+// capacity is read from global memory instead.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int seg_base[9], seg_len[9], seg_ok[9];
     __shared__ int shm[kBlock / 32];
     __shared__ double shs[kBlock / 32];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
-    int64_t s = gtid();
-    int m = 0;
-    if (s < a.n) {
-        float4 ci = a.cand[s];
-        int i = __float_as_int(ci.w);
+    const int Gx = a.G[0], Gy = a.G[1], Gz = a.G[2];
+    const int capr = a.cap_row;
+    float4* s_cand = reinterpret_cast<float4*>(smem);                          // [9][capr]
+    int* s_start = reinterpret_cast<int*>(smem + (size_t)9 * capr * sizeof(float4));  // [9][Gx + 1]
+    const int y = blockIdx.x % Gy, z = blockIdx.x / Gy;
+    if (threadIdx.x < 9) {
+        int k = threadIdx.x;
+        int yy = wrap_add(y, k % 3 - 1, Gy), zz = wrap_add(z, k / 3 - 1, Gz);
+        int rb = (zz * Gy + yy) * Gx;
+        int b = a.cell_start[rb], e = min(a.cell_start[rb + Gx], (int)a.n);
+        seg_base[k] = b;
+        seg_len[k] = max(e - b, 0);
+        seg_ok[k] = (e - b) <= capr;
+    }
+    __syncthreads();
+    for (int k = 0; k < 9; k++) {
+        int yy = wrap_add(y, k % 3 - 1, Gy), zz = wrap_add(z, k / 3 - 1, Gz);
+        int rb = (zz * Gy + yy) * Gx;
+        const int b = seg_base[k];
+        for (int x = threadIdx.x; x <= Gx; x += blockDim.x) s_start[k * (Gx + 1) + x] = a.cell_start[rb + x] - b;
+        if (seg_ok[k])
+            for (int t = threadIdx.x; t < seg_len[k]; t += blockDim.x) s_cand[k * capr + t] = __ldg(a.cand + b + t);
+    }
+    __syncthreads();
+    int mmax = 0;
+    long long msum = 0;
+    const int rowlen = seg_len[4], rowbase = seg_base[4];
+    for (int loc = threadIdx.x; loc < rowlen; loc += blockDim.x) {
+        const float4 ci = seg_ok[4] ? s_cand[4 * capr + loc] : __ldg(a.cand + rowbase + loc);
+        const int i = __float_as_int(ci.w);
         int cx, cy, cz;
         unpack_cell(a.cell[i], cx, cy, cz);
         int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
-        const float qxm = ci.x + a.wf[0], qxp = ci.x - a.wf[0];  // x seen from cells x-1 and x+1
-        const bool inner = cx >= 1 && cx <= a.G[0] - 2;
-        const int xm = wrap_add(cx, -1, a.G[0]), xp = wrap_add(cx, 1, a.G[0]);
-        for (int dz = -1; dz <= 1; dz++) {
-            int z = wrap_add(cz, dz, a.G[2]);
-            float qz = ci.z - (float)dz * a.wf[2];
-            for (int dy = -1; dy <= 1; dy++) {
-                int y = wrap_add(cy, dy, a.G[1]);
-                float qy = ci.y - (float)dy * a.wf[1];
-                unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
-                int row = (z * a.G[1] + y) * a.G[0];
-                // cells x-1, x, x+1 of this row: [r0, r1), [r1, r2), [r2, r3)
-                // when contiguous, else three separate ranges
-                int r0, r1, r2, r3, e0, f0;
-                if (inner) {
-                    r0 = a.cell_start[row + cx - 1];
-                    r1 = a.cell_start[row + cx];
-                    r2 = a.cell_start[row + cx + 1];
-                    r3 = a.cell_start[row + cx + 2];
-                    e0 = r1;
-                    f0 = r2;
-                } else {
-                    r0 = a.cell_start[row + xm];
-                    e0 = a.cell_start[row + xm + 1];
-                    r1 = a.cell_start[row + cx];
-                    r2 = a.cell_start[row + cx + 1];
-                    f0 = a.cell_start[row + xp];
-                    r3 = a.cell_start[row + xp + 1];
-                }
-                // pieces: [r0, e0) is x-1, [r1, r2) is x, [f0, r3) is x+1
-                for (int piece = 0; piece < 3; piece++) {
-                    int lo = piece == 0 ? r0 : (piece == 1 ? r1 : f0);
-                    int hi = piece == 0 ? e0 : (piece == 1 ? r2 : r3);
-                    hi = min(hi, (int)a.n);
-                    const float qx = piece == 0 ? qxm : (piece == 1 ? ci.x : qxp);
-                    const unsigned code = (unsigned)piece | code_yz;
-                    for (int t = lo; t < hi; t++) {
-                        if (t == s) continue;
-                        float4 pj = __ldg(a.cand + t);
-                        float ex = qx - pj.x;
-                        float ey = qy - pj.y;
-                        float ez = qz - pj.z;
-                        float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        int j = __float_as_int(pj.w);
-                        bool take = rr < a.rn2_lo;
-                        if (!take && rr < a.rn2_hi) take = within_rn_fp64(a, i, j, piece - 1, dy, dz);
-                        if (take) {
-                            if (m < a.cap) col[(size_t)m * 32] = j | (int)(code << kCodeShift);
-                            m++;
-                        }
+        const float qxs[3] = {ci.x + a.wf[0], ci.x, ci.x - a.wf[0]};  // seen from cells x-1, x, x+1
+        int m = 0;
+        for (int k = 0; k < 9; k++) {
+            const int dy = k % 3 - 1, dz = k / 3 - 1;
+            const float qy = ci.y - (float)dy * a.wf[1];
+            const float qz = ci.z - (float)dz * a.wf[2];
+            const unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
+            const int* st = s_start + k * (Gx + 1);
+            const bool ok = seg_ok[k] != 0;
+            const float4* seg = ok ? s_cand + k * capr : a.cand + seg_base[k];
+            for (int piece = 0; piece < 3; piece++) {
+                const int xc = wrap_add(cx, piece - 1, Gx);
+                const int lo = st[xc], hi = min(st[xc + 1], seg_len[k]);
+                const float qx = qxs[piece];
+                const unsigned code = (unsigned)piece | code_yz;
+                for (int t = lo; t < hi; t++) {
+                    if (k == 4 && t == loc) continue;
+                    const float4 pj = ok ? seg[t] : __ldg(seg + t);
+                    const float ex = qx - pj.x;
+                    const float ey = qy - pj.y;
+                    const float ez = qz - pj.z;
+                    const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const int j = __float_as_int(pj.w);
+                    bool take = rr < a.rn2_lo;
+                    if (!take && rr < a.rn2_hi) take = within_rn_fp64(a, i, j, piece - 1, dy, dz);
+                    if (take) {
+                        if (m < a.cap) col[(size_t)m * 32] = j | (int)(code << kCodeShift);
+                        m++;
                     }
                 }
             }
@@ -788,9 +857,11 @@ __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
             atomicOr(&C->error, kErrOverflow);
             atomicMax(&C->need_cap, m);
         }
+        mmax = max(mmax, m);
+        msum += m;
     }
-    int bm = block_max_int(m, shm);
-    double bs = block_sum((double)m, shs);
+    int bm = block_max_int(mmax, shm);
+    double bs = block_sum((double)msum, shs);
     if (threadIdx.x == 0) {
         atomicMax(&C->max_nn, bm);
         atomicAdd((unsigned long long*)&C->list_entries, (unsigned long long)bs);
@@ -894,8 +965,11 @@ __global__ void __launch_bounds__(kBlock) k_step(Args<P> a, int mode, cudaGraphC
     using vel = typename P::vel;
     using pos4 = typename P::pos4;
     __shared__ double shs[kBlock / 32];
+    __shared__ pos4 s_shift[64];
+    __shared__ typename Queue<P>::item s_queue[kCells ? 1 : Queue<P>::kSlots * kBlock];
     Counters* C = a.ctr;
-    const View vw = load_view(C);
+    if constexpr (!kCells) fill_shift_table<P>(a, s_shift);
+    const View vw = load_view(C);  // also orders the table fill before its use
     const int err = vw.err;
     const long long left = vw.left;
     const int par = vw.par;
@@ -916,10 +990,10 @@ __global__ void __launch_bounds__(kBlock) k_step(Args<P> a, int mode, cudaGraphC
         typename AccOf<P>::type acc;
         if (kFinal && energy) {
             if constexpr (kCells) forces_from_cells<P, kFinal>(a, (int)i, qx, qy, qz, pc, acc);
-            else forces_from_list<P, kFinal>(a, (int)i, qx, qy, qz, pc, acc);
+            else forces_from_list<P, kFinal>(a, (int)i, qx, qy, qz, pc, s_shift, s_queue, acc);
         } else {
             if constexpr (kCells) forces_from_cells<P, false>(a, (int)i, qx, qy, qz, pc, acc);
-            else forces_from_list<P, false>(a, (int)i, qx, qy, qz, pc, acc);
+            else forces_from_list<P, false>(a, (int)i, qx, qy, qz, pc, s_shift, s_queue, acc);
         }
         close = acc.close != 0;
         real fx = acc.force_x(), fy = acc.force_y(), fz = acc.force_z();
