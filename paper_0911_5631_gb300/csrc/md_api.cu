@@ -232,8 +232,6 @@ struct Sim : SimBase {
         }
         kt = make_kernel_table<P>();
         fill_scalars(n);
-        if (!prm.cell_list_only)
-            MD_CUDA(cudaFuncSetAttribute(kt.build, cudaFuncAttributeMaxDynamicSharedMemorySize, a.build_smem));
         int r = allocate();
         if (r) return r;
         return MD_OK;
@@ -275,18 +273,6 @@ struct Sim : SimBase {
         a.thr2f = (float)(a.thr2 * (1.0 - 1e-5));
         a.close2 = 0.08;
         a.close2f = 0.08f;
-        // shared-memory staging of the neighbour build: 3 x 3 rows of cells,
-        // sized for 1.4 times the mean row plus slack (longer rows fall back
-        // to global loads), capped at the opt-in shared memory of a block
-        double mean_row = (double)n / ((double)plan.G[1] * plan.G[2]);
-        int capr = ((int)(mean_row * 1.4) + 64 + 31) & ~31;
-        int per_k = (int)sizeof(float4) * capr;
-        int starts = 9 * (plan.G[0] + 1) * (int)sizeof(int);
-        int limit = 200 * 1024;
-        if (9 * per_k + starts > limit) capr = ((limit - starts) / (9 * (int)sizeof(float4))) & ~31;
-        if (capr < 32) capr = 32;
-        a.cap_row = capr;
-        a.build_smem = 9 * (int)sizeof(float4) * capr + starts;
     }
 
     int allocate() {
@@ -345,14 +331,6 @@ struct Sim : SimBase {
     }
 
     unsigned grid_atoms() const { return (unsigned)a.nblocks; }
-    unsigned grid_rows() const { return (unsigned)(a.G[1] * a.G[2]); }
-
-    template <class... T>
-    cudaError_t launch_smem(void* f, unsigned grid, unsigned block, int smem, T&... args) {
-        void* p[] = {(void*)&args...};
-        launches++;
-        return cudaLaunchKernel(f, dim3(grid), dim3(block), p, (size_t)smem, stream);
-    }
     unsigned grid_cells() const { return (unsigned)((a.ncells + kBlock - 1) / kBlock); }
     unsigned grid_scatter() const {
         int64_t m = a.n > a.ncells ? a.n : a.ncells;
@@ -375,7 +353,7 @@ struct Sim : SimBase {
         MD_CUDA(launch(kt.cellsort, grid_cells(), kBlock, a, g));
         MD_CUDA(launch(kt.gather, grid_atoms(), kBlock, a, g));
         MD_CUDA(launch(kt.commit, grid_atoms(), kBlock, a, g));
-        if (!prm.cell_list_only) MD_CUDA(launch_smem(kt.build, grid_rows(), kBlock, a.build_smem, a, g));
+        if (!prm.cell_list_only) MD_CUDA(launch(kt.build, grid_atoms(), kBlock, a, g));
         MD_CUDA(launch(kt.rebuild_done, 1, 32, a, g));
         return MD_OK;
     }
@@ -415,21 +393,6 @@ struct Sim : SimBase {
         return cudaGraphAddNode(out, g, dep, nullptr, dep ? 1 : 0, &np);
     }
 
-    template <class... T>
-    cudaError_t add_kernel_smem(cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNode_t* out, void* f, unsigned grid,
-                                unsigned block, int smem, T&... args) {
-        void* p[] = {(void*)&args...};
-        NodeParams buf;
-        cudaGraphNodeParams& np = buf.get();
-        np.type = cudaGraphNodeTypeKernel;
-        np.kernel.func = f;
-        np.kernel.gridDim = dim3(grid);
-        np.kernel.blockDim = dim3(block);
-        np.kernel.sharedMemBytes = (unsigned)smem;
-        np.kernel.kernelParams = p;
-        return cudaGraphAddNode(out, g, dep, nullptr, dep ? 1 : 0, &np);
-    }
-
     int build_body(cudaGraph_t body) {
         int g = 0;
         cudaGraphNode_t prev = nullptr, cur = nullptr;
@@ -446,7 +409,7 @@ struct Sim : SimBase {
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.gather, grid_atoms(), kBlock, a, g)));
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.commit, grid_atoms(), kBlock, a, g)));
         if (!prm.cell_list_only)
-            MD_CUDA(chain(add_kernel_smem(body, &prev, &cur, kt.build, grid_rows(), kBlock, a.build_smem, a, g)));
+            MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.build, grid_atoms(), kBlock, a, g)));
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.rebuild_done, 1, 32, a, g)));
         return MD_OK;
     }

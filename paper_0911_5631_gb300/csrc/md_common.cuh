@@ -92,8 +92,6 @@ struct Args {
     int nblocks;        // ceil(n / kBlock)
     int cell_list_only;
     int reorder_interval;
-    int cap_row;        // atoms per cell row the neighbour build stages in shared memory
-    int build_smem;     // dynamic shared memory of the neighbour build (bytes)
 
     double L[3], hL[3], invL[3], invW[3];
     double w[3];        // cell widths

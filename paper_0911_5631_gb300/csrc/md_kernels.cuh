@@ -770,84 +770,76 @@ __device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int 
     return r2 < a.rn2;
 }
 
-// Neighbour-list build (Sec. 3.4).  One block per row of cells (fixed c_y,
-// c_z; all c_x): the block first stages the cell-ordered FP32 coordinates
-// and the cell starts of the 3 x 3 neighbouring rows in shared memory, then
-// each thread takes one atom of the row and scans the 27 cells around the
-// atom's cell from shared memory, recording every j != i with r < r_n in
-// its column together with the cell-offset code.  The decision is the exact
-// FP64 criterion: FP32 coordinates settle every candidate outside a narrow
-// band around r_n^2, the FP64 test the rest.  A row longer than the staging
-// capacity is read from global memory instead.
+// Neighbour-list build (Sec. 3.4): for the atom in cell-ordered slot s, scan
+// the 27 cells around its cell -- as 9 rows of 3 cells, contiguous in cell
+// order unless the row wraps -- and record every j != i with r < r_n in its
+// column together with the cell-offset code.  The decision is the exact
+// FP64 criterion; FP32 coordinates settle every candidate outside a narrow
+// band around r_n^2 and the FP64 test the rest.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int seg_base[9], seg_len[9], seg_ok[9];
     __shared__ int shm[kBlock / 32];
     __shared__ double shs[kBlock / 32];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
-    const int Gx = a.G[0], Gy = a.G[1], Gz = a.G[2];
-    const int capr = a.cap_row;
-    float4* s_cand = reinterpret_cast<float4*>(smem);                          // [9][capr]
-    int* s_start = reinterpret_cast<int*>(smem + (size_t)9 * capr * sizeof(float4));  // [9][Gx + 1]
-    const int y = blockIdx.x % Gy, z = blockIdx.x / Gy;
-    if (threadIdx.x < 9) {
-        int k = threadIdx.x;
-        int yy = wrap_add(y, k % 3 - 1, Gy), zz = wrap_add(z, k / 3 - 1, Gz);
-        int rb = (zz * Gy + yy) * Gx;
-        int b = a.cell_start[rb], e = min(a.cell_start[rb + Gx], (int)a.n);
-        seg_base[k] = b;
-        seg_len[k] = max(e - b, 0);
-        seg_ok[k] = (e - b) <= capr;
-    }
-    __syncthreads();
-    for (int k = 0; k < 9; k++) {
-        int yy = wrap_add(y, k % 3 - 1, Gy), zz = wrap_add(z, k / 3 - 1, Gz);
-        int rb = (zz * Gy + yy) * Gx;
-        const int b = seg_base[k];
-        for (int x = threadIdx.x; x <= Gx; x += blockDim.x) s_start[k * (Gx + 1) + x] = a.cell_start[rb + x] - b;
-        if (seg_ok[k])
-            for (int t = threadIdx.x; t < seg_len[k]; t += blockDim.x) s_cand[k * capr + t] = __ldg(a.cand + b + t);
-    }
-    __syncthreads();
-    int mmax = 0;
-    long long msum = 0;
-    const int rowlen = seg_len[4], rowbase = seg_base[4];
-    for (int loc = threadIdx.x; loc < rowlen; loc += blockDim.x) {
-        const float4 ci = seg_ok[4] ? s_cand[4 * capr + loc] : __ldg(a.cand + rowbase + loc);
-        const int i = __float_as_int(ci.w);
+    int64_t s = gtid();
+    int m = 0;
+    if (s < a.n) {
+        float4 ci = a.cand[s];
+        int i = __float_as_int(ci.w);
         int cx, cy, cz;
         unpack_cell(a.cell[i], cx, cy, cz);
         int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
-        const float qxs[3] = {ci.x + a.wf[0], ci.x, ci.x - a.wf[0]};  // seen from cells x-1, x, x+1
-        int m = 0;
-        for (int k = 0; k < 9; k++) {
-            const int dy = k % 3 - 1, dz = k / 3 - 1;
-            const float qy = ci.y - (float)dy * a.wf[1];
-            const float qz = ci.z - (float)dz * a.wf[2];
-            const unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
-            const int* st = s_start + k * (Gx + 1);
-            const bool ok = seg_ok[k] != 0;
-            const float4* seg = ok ? s_cand + k * capr : a.cand + seg_base[k];
-            for (int piece = 0; piece < 3; piece++) {
-                const int xc = wrap_add(cx, piece - 1, Gx);
-                const int lo = st[xc], hi = min(st[xc + 1], seg_len[k]);
-                const float qx = qxs[piece];
-                const unsigned code = (unsigned)piece | code_yz;
-                for (int t = lo; t < hi; t++) {
-                    if (k == 4 && t == loc) continue;
-                    const float4 pj = ok ? seg[t] : __ldg(seg + t);
-                    const float ex = qx - pj.x;
-                    const float ey = qy - pj.y;
-                    const float ez = qz - pj.z;
-                    const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    const int j = __float_as_int(pj.w);
-                    bool take = rr < a.rn2_lo;
-                    if (!take && rr < a.rn2_hi) take = within_rn_fp64(a, i, j, piece - 1, dy, dz);
-                    if (take) {
-                        if (m < a.cap) col[(size_t)m * 32] = j | (int)(code << kCodeShift);
-                        m++;
+        const float qxm = ci.x + a.wf[0], qxp = ci.x - a.wf[0];  // x seen from cells x-1 and x+1
+        const bool inner = cx >= 1 && cx <= a.G[0] - 2;
+        const int xm = wrap_add(cx, -1, a.G[0]), xp = wrap_add(cx, 1, a.G[0]);
+        for (int dz = -1; dz <= 1; dz++) {
+            int z = wrap_add(cz, dz, a.G[2]);
+            float qz = ci.z - (float)dz * a.wf[2];
+            for (int dy = -1; dy <= 1; dy++) {
+                int y = wrap_add(cy, dy, a.G[1]);
+                float qy = ci.y - (float)dy * a.wf[1];
+                unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
+                int row = (z * a.G[1] + y) * a.G[0];
+                // cells x-1, x, x+1 of this row: [r0, r1), [r1, r2), [r2, r3)
+                // when contiguous, else three separate ranges
+                int r0, r1, r2, r3, e0, f0;
+                if (inner) {
+                    r0 = a.cell_start[row + cx - 1];
+                    r1 = a.cell_start[row + cx];
+                    r2 = a.cell_start[row + cx + 1];
+                    r3 = a.cell_start[row + cx + 2];
+                    e0 = r1;
+                    f0 = r2;
+                } else {
+                    r0 = a.cell_start[row + xm];
+                    e0 = a.cell_start[row + xm + 1];
+                    r1 = a.cell_start[row + cx];
+                    r2 = a.cell_start[row + cx + 1];
+                    f0 = a.cell_start[row + xp];
+                    r3 = a.cell_start[row + xp + 1];
+                }
+                // pieces: [r0, e0) is x-1, [r1, r2) is x, [f0, r3) is x+1
+                for (int piece = 0; piece < 3; piece++) {
+                    int lo = piece == 0 ? r0 : (piece == 1 ? r1 : f0);
+                    int hi = piece == 0 ? e0 : (piece == 1 ? r2 : r3);
+                    hi = min(hi, (int)a.n);
+                    const float qx = piece == 0 ? qxm : (piece == 1 ? ci.x : qxp);
+                    const unsigned code = (unsigned)piece | code_yz;
+                    for (int t = lo; t < hi; t++) {
+                        if (t == s) continue;
+                        float4 pj = __ldg(a.cand + t);
+                        float ex = qx - pj.x;
+                        float ey = qy - pj.y;
+                        float ez = qz - pj.z;
+                        float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        int j = __float_as_int(pj.w);
+                        bool take = rr < a.rn2_lo;
+                        if (!take && rr < a.rn2_hi) take = within_rn_fp64(a, i, j, piece - 1, dy, dz);
+                        if (take) {
+                            if (m < a.cap) col[(size_t)m * 32] = j | (int)(code << kCodeShift);
+                            m++;
+                        }
                     }
                 }
             }
@@ -857,11 +849,9 @@ __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
             atomicOr(&C->error, kErrOverflow);
             atomicMax(&C->need_cap, m);
         }
-        mmax = max(mmax, m);
-        msum += m;
     }
-    int bm = block_max_int(mmax, shm);
-    double bs = block_sum((double)msum, shs);
+    int bm = block_max_int(m, shm);
+    double bs = block_sum((double)m, shs);
     if (threadIdx.x == 0) {
         atomicMax(&C->max_nn, bm);
         atomicAdd((unsigned long long*)&C->list_entries, (unsigned long long)bs);
