@@ -220,6 +220,40 @@ const char* md_last_error(const md_handle* h);
  * float->int64 and int64->float.  MD_ENODEV without a GPU. */
 int md_selftest(int64_t n, int64_t failures[4]);
 
+/* ---- forces without device allocation --------------------------------
+ * The paper has no counterpart to this call; it serves callers that may
+ * not allocate device memory -- code that runs inside a memory pool or
+ * budget it does not own, or on a path where cudaMalloc/cudaFree must not
+ * run because they synchronise the whole device.
+ *
+ * md_forces_noalloc computes, in FP64, the forces of one configuration and
+ * its potential energy and virial: positions are wrapped, binned into cells
+ * of width >= rc and the pair term of Eq. (1) plus ushift (NaN: the
+ * automatic shift of md_params.ushift) is summed over the 27 neighbouring
+ * cells -- the same numbers md_set_state + md_get_forces + md_measure give
+ * for the FP64 form, up to summation order.
+ *   box  region edges; each must hold at least 3 cells of width rc
+ *   pos  device, n x 3 doubles;  f  device, n x 3 doubles (out)
+ *   pe_vir  device, 2 doubles (out): U and W = sum over pairs of r.f
+ *   stream  cudaStream_t the work is queued on (NULL: legacy default
+ *           stream); the call returns without synchronising it.
+ * It allocates nothing: its working memory is one fixed scratch area of
+ * MD_NOALLOC_SCRATCH_BYTES inside the library (a static device array that
+ * every GPU which loads the library keeps until the process exits), so
+ * n <= MD_NOALLOC_MAX_ATOMS and the cell count <= MD_NOALLOC_MAX_CELLS;
+ * larger inputs return MD_EINVAL (message in md_last_error(NULL)).
+ * The first call on a device looks up the scratch address on that device
+ * (the current device); make that first call outside any stream capture.
+ * All calls share the scratch area, which keeps the previous call's
+ * contents (the call clears what must start at zero): calls whose work
+ * overlaps on the GPU -- on different streams or from different host
+ * threads -- race and return wrong results. */
+#define MD_NOALLOC_MAX_ATOMS 65536
+#define MD_NOALLOC_MAX_CELLS 65536
+#define MD_NOALLOC_SCRATCH_BYTES (4u << 20)
+int md_forces_noalloc(const double box[3], int64_t n, double rc, double ushift, const double* pos,
+                      double* f, double* pe_vir, void* stream);
+
 /* Static description of an error code. */
 const char* md_strerror(int code);
 

@@ -132,8 +132,13 @@ SIGNATURES = [
     ("md_destroy", None, [_H]),
     ("md_last_error", C.c_char_p, [_H]),
     ("md_selftest", C.c_int, [C.c_int64, C.POINTER(C.c_int64)]),
+    ("md_forces_noalloc", C.c_int, [_D3, C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
     ("md_strerror", C.c_char_p, [C.c_int]),
 ]
+
+MD_NOALLOC_MAX_ATOMS = 65536
+MD_NOALLOC_MAX_CELLS = 65536
 
 _lib = None
 _lock = threading.Lock()
@@ -288,6 +293,16 @@ def md_selftest(n=1 << 22):
     f = (C.c_int64 * 4)()
     _check(lib().md_selftest(int(n), f))
     return list(f)
+
+
+def md_forces_noalloc(box, n, rc, pos_ptr: int, f_ptr: int, pe_vir_ptr: int, ushift=None, stream=None):
+    """Forces, U and W of one configuration without any device allocation
+    (device pointers in and out; see include/md.h)."""
+    b, bp = _box(box)
+    code = lib().md_forces_noalloc(bp, int(n), float(rc), math.nan if ushift is None else float(ushift),
+                                   C.c_void_p(pos_ptr), C.c_void_p(f_ptr), C.c_void_p(pe_vir_ptr),
+                                   None if stream is None else C.c_void_p(int(stream)))
+    return _check(code)
 
 
 def md_strerror(code) -> str:

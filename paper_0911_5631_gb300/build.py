@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-UNITS = ["md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_api.cu"]
+UNITS = ["md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_api.cu", "md_noalloc.cu"]
 HEADERS = ["md_common.cuh", "md_kernels.cuh", "md_table.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -809,6 +809,10 @@ struct Sim : SimBase {
 
 }  // namespace
 
+namespace md {
+__attribute__((visibility("hidden"))) void set_call_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace md
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
