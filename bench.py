@@ -259,6 +259,11 @@ def run_ours(args):
     clk = clocks.stop()
     m1 = sim.measure()
     st1 = sim.kernel_stats()
+    # the timed region must have advanced the simulation by exactly the
+    # steps it claims
+    done = m1["step"] - m0["step"]
+    if done != args.chunk * args.steps:
+        raise RuntimeError("timed region advanced %d MD steps, expected %d" % (done, args.chunk * args.steps))
     value, ms = job_throughput(n * args.chunk * args.steps, ms_local, dist, "cuda")
     launches = st1["launches"] - st0["launches"]
 
@@ -280,6 +285,8 @@ def run_ours(args):
                 "peak_kind": peak_kind, "kernel": "k_step (force + integrate, mixed)",
                 "kernel_ms_per_launch": kms / kl if kl else None,
                 "algorithmic_bytes_per_launch": kbytes / kl if kl else None}
+    rb = p1["rebuilds_timed"] - p0["rebuilds_timed"]
+    rebuild_ms = (p1["rebuild_ms"] - p0["rebuild_ms"]) / rb if rb else None
     list_entries = m1["list_entries"]
     rebuilds = m1["rebuilds"] - m0["rebuilds"]
 
@@ -353,6 +360,7 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single"},
             "gpu_launches": int(launches),
             "rebuilds_in_timed_region": int(rebuilds),
+            "rebuild_ms_per_branch": rebuild_ms,
             "neighbours_per_atom": list_entries / n,
             "roofline": roofline,
             "fp64_form": fp64,

@@ -130,6 +130,8 @@ typedef struct md_kernel_stats_t {
     double step_kernel_ms;    /* summed CUDA-event time of those launches       */
     int64_t step_kernel_atoms;/* atoms processed by them                        */
     int64_t step_kernel_bytes;/* algorithmic bytes moved by them (see md_plan)  */
+    int64_t rebuilds_timed;   /* rebuild branches (Sec. 3.1 (b)) timed below    */
+    double rebuild_ms;        /* their summed CUDA-event time                   */
 } md_kernel_stats_t;
 
 typedef struct md_handle md_handle;

@@ -103,6 +103,8 @@ class md_kernel_stats_t(C.Structure):
         ("step_kernel_ms", C.c_double),
         ("step_kernel_atoms", C.c_int64),
         ("step_kernel_bytes", C.c_int64),
+        ("rebuilds_timed", C.c_int64),
+        ("rebuild_ms", C.c_double),
     ]
 
 

@@ -181,6 +181,8 @@ struct Sim : SimBase {
     int64_t rebuilds_at_mark = 0;
     double step_ms = 0.0;
     int64_t step_launches = 0;
+    double rebuild_ms = 0.0;
+    int64_t rebuilds_timed = 0;
     int64_t step_atoms = 0;
     int64_t step_bytes = 0;
 
@@ -273,6 +275,9 @@ struct Sim : SimBase {
         a.thr2f = (float)(a.thr2 * (1.0 - 1e-5));
         a.close2 = 0.08;
         a.close2f = 0.08f;
+        // |f_d| = (f/r) |d_d| < (f/r) r_c for an interacting pair; 2000 leaves
+        // room for the rounding of the product below 2^11
+        a.fix_small_fr = (float)(2000.0 / std::sqrt(a.rc2));
     }
 
     int allocate() {
@@ -477,8 +482,8 @@ struct Sim : SimBase {
                 launches += 2;
             }
         } else {
-            if (profiling && (int64_t)ev.size() < 2 * nsteps) {
-                while ((int64_t)ev.size() < 2 * nsteps) {
+            if (profiling && (int64_t)ev.size() < 4 * nsteps) {
+                while ((int64_t)ev.size() < 4 * nsteps) {
                     cudaEvent_t e;
                     MD_CUDA(cudaEventCreate(&e));
                     ev.push_back(e);
@@ -487,23 +492,34 @@ struct Sim : SimBase {
             // Stream launches: the host reads the device rebuild flag before
             // each step, so only rebuilds that are due are launched (one
             // round trip per step; this path serves profiling and checks).
+            std::vector<char> rebuilt(profiling ? nsteps : 0, 0);
             for (int64_t s = 0; s < nsteps; s++) {
                 int flag = 0;
                 MD_CUDA(cudaMemcpyAsync(&flag, &a.ctr->rebuild_flag, sizeof(int), cudaMemcpyDeviceToHost, stream));
                 MD_CUDA(cudaStreamSynchronize(stream));
+                if (profiling && flag) {
+                    rebuilt[s] = 1;
+                    MD_CUDA(cudaEventRecord(ev[4 * s + 2], stream));
+                }
                 int r = flag ? rebuild_eager(0) : MD_OK;
                 if (r) return r;
-                if (profiling) MD_CUDA(cudaEventRecord(ev[2 * s], stream));
+                if (profiling && flag) MD_CUDA(cudaEventRecord(ev[4 * s + 3], stream));
+                if (profiling) MD_CUDA(cudaEventRecord(ev[4 * s], stream));
                 r = step_kernel_eager(kModeAuto, s + 1 == nsteps);
                 if (r) return r;
-                if (profiling) MD_CUDA(cudaEventRecord(ev[2 * s + 1], stream));
+                if (profiling) MD_CUDA(cudaEventRecord(ev[4 * s + 1], stream));
             }
             if (profiling) {
                 MD_CUDA(cudaStreamSynchronize(stream));
                 for (int64_t s = 0; s < nsteps; s++) {
                     float ms = 0.f;
-                    MD_CUDA(cudaEventElapsedTime(&ms, ev[2 * s], ev[2 * s + 1]));
+                    MD_CUDA(cudaEventElapsedTime(&ms, ev[4 * s], ev[4 * s + 1]));
                     step_ms += ms;
+                    if (rebuilt[s]) {
+                        MD_CUDA(cudaEventElapsedTime(&ms, ev[4 * s + 2], ev[4 * s + 3]));
+                        rebuild_ms += ms;
+                        rebuilds_timed++;
+                    }
                 }
                 step_launches += nsteps;
             }
@@ -794,6 +810,8 @@ struct Sim : SimBase {
         out->step_kernel_atoms = step_launches * a.n;
         int64_t base = P::kFp64 ? 188 : 120;
         out->step_kernel_bytes = step_launches * (base * a.n + 4 * c.list_entries);
+        out->rebuilds_timed = rebuilds_timed;
+        out->rebuild_ms = rebuild_ms;
         return MD_OK;
     }
 

@@ -9,6 +9,7 @@ namespace md {
 
 // Threads per block for every per-atom / per-slot kernel.
 constexpr int kBlock = 256;
+constexpr int kStageRows = 12;  // neighbour-list rows a step-kernel warp copies to shared memory
 // Elements per block of the cell-count scan (kBlock threads x 8).
 constexpr int kScanTile = 2048;
 // Largest neighbour capacity of the mixed form (its fixed-point partial
@@ -109,6 +110,7 @@ struct Args {
     double thr2;        // (skin/2)^2
     float thr2f;
     float close2f;      // pairs closer than this flag kErrClose
+    float fix_small_fr; // mixed form: a pair with f/r below this has every force component under 2^11
     double close2;
 
     // per-atom state, storage order

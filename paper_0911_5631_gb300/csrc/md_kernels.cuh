@@ -55,6 +55,14 @@ __device__ __forceinline__ bool last_block_done(Counters* C) {
 
 // Counters that steer a kernel, read once per block so that every thread of
 // the block takes the same branch.
+// Asynchronous 16-byte global->shared copy (L2 only) and the wait for all
+// of this thread's outstanding copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 struct View {
     int err;
     int par;
@@ -104,7 +112,8 @@ __device__ __forceinline__ void unpack_cell(int p, int& cx, int& cy, int& cz) {
     cy = (p >> 10) & 1023;
     cz = (p >> 20) & 1023;
 }
-// Scalar cell index c = (c_z G_y + c_y) G_x + c_x (0-based form of Sec. 3.1).
+// Scalar cell index c = (c_z G_y + c_y) G_x + c_x (0-based form of Sec. 3.1),
+// the cell id reported to callers.
 __device__ __forceinline__ int linear_cell(int cx, int cy, int cz, const int G[3]) {
     return (cz * G[1] + cy) * G[0] + cx;
 }
@@ -112,6 +121,37 @@ __device__ __forceinline__ int linear_of_packed(int p, const int G[3]) {
     int cx, cy, cz;
     unpack_cell(p, cx, cy, cz);
     return linear_cell(cx, cy, cz, G);
+}
+
+// Storage order of the cells: the order of count, cell_start and of every
+// cell-ordered array.  Sec. 3.5 only asks that the atoms of a cell sit
+// together; which cell comes next is free.  Here the (y, z) cross-section is
+// cut into tiles of 4 x 4 cells (narrower at the high faces), each tile
+// extended along x is a pencil, pencils follow one another tile row by tile
+// row, and a pencil lists its cells one x slice after the other.  A thread
+// block's atoms then fill a few slices of one pencil, so they and their
+// 27-cell neighbourhoods span a few kilobytes and the neighbour reads of the
+// force and build kernels mostly hit in L1.  For fixed (c_y, c_z) the index
+// is base + c_x * stride.
+struct PencilRow {
+    int base, stride;
+};
+__device__ __forceinline__ PencilRow pencil_row(int cy, int cz, const int G[3]) {
+    const int y0 = cy & ~3, z0 = cz & ~3;
+    const int hy = min(4, G[1] - y0), hz = min(4, G[2] - z0);
+    PencilRow r;
+    r.stride = hy * hz;
+    r.base = (z0 * G[1] + y0 * hz) * G[0] + (cz - z0) * hy + (cy - y0);
+    return r;
+}
+__device__ __forceinline__ int cell_index(int cx, int cy, int cz, const int G[3]) {
+    const PencilRow r = pencil_row(cy, cz, G);
+    return r.base + cx * r.stride;
+}
+__device__ __forceinline__ int cell_index_of_packed(int p, const int G[3]) {
+    int cx, cy, cz;
+    unpack_cell(p, cx, cy, cz);
+    return cell_index(cx, cy, cz, G);
 }
 
 __device__ __forceinline__ int wrap_add(int c, int d, int G) {
@@ -186,23 +226,83 @@ __device__ __forceinline__ float from_fix(long long q) {
 // exact, so the three sums are exact and independent of the order of the
 // terms, and add(-g) subtracts exactly what add(g) adds.  value()
 // assembles the int64 sum.  With at most 512 terms no partial sum leaves
-// int32.
+// int32.  For |g| <= 2^11 the first chunk is zero and its remainder is g
+// itself, so add_small(g) -- the last two chunks alone -- adds exactly
+// what add(g) adds.
+constexpr float kFixMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int kFixMagicBits = 0x4B400000;  // its bit pattern
+constexpr float kFixSmall = 2048.0f;       // add_small is exact up to this magnitude
 struct Fix {
     int a = 0, b = 0, c = 0;
+    __device__ __forceinline__ void add_small(float g) {
+        float s2 = fmaf(g, 1024.0f, kFixMagic);
+        b += __float_as_int(s2) - kFixMagicBits;
+        float r2 = fmaf(s2 - kFixMagic, -0x1p-10f, g);
+        float s3 = fmaf(r2, 4294967296.0f, kFixMagic);
+        c += __float_as_int(s3) - kFixMagicBits;
+    }
     __device__ __forceinline__ void add(float g) {
-        const float M = 12582912.0f;  // 1.5 * 2^23
-        const int MB = 0x4B400000;    // its bit pattern
-        float s1 = fmaf(g, 0x1p-12f, M);
-        a += __float_as_int(s1) - MB;
-        float r1 = fmaf(s1 - M, -4096.0f, g);
-        float s2 = fmaf(r1, 1024.0f, M);
-        b += __float_as_int(s2) - MB;
-        float r2 = fmaf(s2 - M, -0x1p-10f, r1);
-        float s3 = fmaf(r2, 4294967296.0f, M);
-        c += __float_as_int(s3) - MB;
+        float s1 = fmaf(g, 0x1p-12f, kFixMagic);
+        a += __float_as_int(s1) - kFixMagicBits;
+        add_small(fmaf(s1 - kFixMagic, -4096.0f, g));
     }
     __device__ __forceinline__ long long value() const {
         return (long long)a * (1ll << 44) + (long long)b * (1ll << 22) + (long long)c;
+    }
+};
+
+// Two binary32 values in one 64-bit register pair, for the packed FP32
+// instructions (add/sub/mul/fma .f32x2) of sm_100-class GPUs: one issue
+// slot computes both halves, each rounded exactly as the scalar
+// instruction would.  The first value sits in the low half.
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float x, float y) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(x), "f"(y));
+    return r;
+}
+__device__ __forceinline__ void f2_get(F2 p, float& x, float& y) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(p.v));
+}
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(x.v), "l"(y.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 x, F2 y) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(x.v), "l"(y.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 x, F2 y) {
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(x.v), "l"(y.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 x, F2 y, F2 z) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(x.v), "l"(y.v), "l"(z.v));
+    return r;
+}
+
+// Two Fix sums advanced together with the packed instructions (the same
+// operations, so the same integers, as two Fix::add_small calls).
+struct Fix2 {
+    Fix x, y;
+    __device__ __forceinline__ void add_small(F2 g) {
+        const F2 M = f2(kFixMagic, kFixMagic);
+        float lo, hi;
+        F2 s2 = f2_fma(g, f2(1024.0f, 1024.0f), M);
+        f2_get(s2, lo, hi);
+        x.b += __float_as_int(lo) - kFixMagicBits;
+        y.b += __float_as_int(hi) - kFixMagicBits;
+        F2 r2 = f2_fma(f2_sub(s2, M), f2(-0x1p-10f, -0x1p-10f), g);
+        F2 s3 = f2_fma(r2, f2(4294967296.0f, 4294967296.0f), M);
+        f2_get(s3, lo, hi);
+        x.c += __float_as_int(lo) - kFixMagicBits;
+        y.c += __float_as_int(hi) - kFixMagicBits;
     }
 };
 
@@ -260,30 +360,48 @@ __device__ __forceinline__ float to_f32(double x) { return cvt::f32(x); }
 // ---------------------------------------------------------------------------
 
 // Mixed form: FP32 pair arithmetic; per-atom sums in int64 fixed point.
+// The x and y components travel as packed pairs.  A pair term whose
+// components all stay within kFixSmall (|f r| < kFixSmall / r_c bounds
+// them, which holds for every r above about 0.75) skips the first,
+// all-zero chunk.
 struct AccMixed {
-    Fix fx, fy, fz, u, w;
+    Fix2 fxy;
+    Fix fz, u, w;
     int close = 0;
     // accumulate one interacting pair (r^2 < r_c^2) at separation d
     template <bool kEnergy>
-    __device__ __forceinline__ void force(const Args<Mixed>& a, float dx, float dy, float dz, float r2) {
+    __device__ __forceinline__ void force(const Args<Mixed>& a, F2 dxy, float dz, float r2) {
         close |= (r2 < a.close2f);
         float ir2 = __fdividef(1.0f, r2);
         float ir6 = ir2 * ir2 * ir2;
         float fr = 48.0f * ir6 * (ir6 - 0.5f) * ir2;
-        fx.add(fr * dx);
-        fy.add(fr * dy);
-        fz.add(fr * dz);
+        F2 gxy = f2_mul(f2(fr, fr), dxy);
+        float gz = fr * dz;
+        if (fr < a.fix_small_fr) {
+            fxy.add_small(gxy);
+            fz.add_small(gz);
+        } else {
+            float gx, gy;
+            f2_get(gxy, gx, gy);
+            fxy.x.add(gx);
+            fxy.y.add(gy);
+            fz.add(gz);
+        }
         if constexpr (kEnergy) {
             u.add(fmaf(4.0f * ir6, ir6 - 1.0f, a.ushiftf));
             w.add(fr * r2);
         }
+    }
+    template <bool kEnergy>
+    __device__ __forceinline__ void force(const Args<Mixed>& a, float dx, float dy, float dz, float r2) {
+        force<kEnergy>(a, f2(dx, dy), dz, r2);
     }
     __device__ __forceinline__ float r2(float dx, float dy, float dz) const { return fmaf(dx, dx, fmaf(dy, dy, dz * dz)); }
     __device__ __forceinline__ bool inside(const Args<Mixed>& a, float r2) const { return r2 < a.rc2f; }
     template <bool kEnergy>
     __device__ __forceinline__ void pair(const Args<Mixed>& a, float dx, float dy, float dz) {
         float rr = r2(dx, dy, dz);
-        if (inside(a, rr)) force<kEnergy>(a, dx, dy, dz, rr);
+        if (inside(a, rr)) force<kEnergy>(a, f2(dx, dy), dz, rr);
     }
     // Per-atom force from the three exact partial sums.  The rounding is
     // not the correctly rounded one, but it is a fixed function of sums
@@ -291,8 +409,8 @@ struct AccMixed {
     __device__ __forceinline__ static float to_force(const Fix& q) {
         return fmaf((float)q.a, 4096.0f, fmaf((float)q.b, 0x1p-10f, (float)q.c * 0x1p-32f));
     }
-    __device__ __forceinline__ float force_x() const { return to_force(fx); }
-    __device__ __forceinline__ float force_y() const { return to_force(fy); }
+    __device__ __forceinline__ float force_x() const { return to_force(fxy.x); }
+    __device__ __forceinline__ float force_y() const { return to_force(fxy.y); }
     __device__ __forceinline__ float force_z() const { return to_force(fz); }
     __device__ __forceinline__ double energy() const { return (double)u.value() * kFixInv; }
     __device__ __forceinline__ double virial() const { return (double)w.value() * kFixInv; }
@@ -339,12 +457,12 @@ template <> struct AccOf<F64> { using type = AccF64; };
 template <class P> struct Queue;
 template <> struct Queue<Mixed> {
     using item = float4;
-    static constexpr int kSlots = 10;
+    static constexpr int kSlots = 6;
     __device__ __forceinline__ static item make(float x, float y, float z, float r2) { return make_float4(x, y, z, r2); }
 };
 template <> struct Queue<F64> {
     using item = double4_32a;
-    static constexpr int kSlots = 5;
+    static constexpr int kSlots = 3;
     __device__ __forceinline__ static item make(double x, double y, double z, double r2) {
         return make_double4_32a(x, y, z, r2);
     }
@@ -371,10 +489,12 @@ __device__ __forceinline__ void fill_shift_table(const Args<P>& a, typename P::p
 // interacting separations; phase 2 evaluates the pair term for the queued
 // pairs only.  A warp thus runs the expensive pair term as often as its
 // busiest atom has interacting partners instead of as often as it has
-// neighbour entries.  Pairs beyond the queue are evaluated at once.
+// neighbour entries.  Pairs beyond the queue are evaluated at once.  The
+// first `staged` rows of the warp's column block are already in shared
+// memory (rows), the rest is read from global memory.
 template <class P, bool kEnergy>
-__device__ __forceinline__ void forces_from_list(const Args<P>& a, int i, typename P::real qx,
-                                                 typename P::real qy, typename P::real qz,
+__device__ __forceinline__ void forces_from_list(const Args<P>& a, int cnt, const int* col, const int* rows, int staged,
+                                                 typename P::real qx, typename P::real qy, typename P::real qz,
                                                  const typename P::pos4* __restrict__ pc,
                                                  const typename P::pos4* __restrict__ shift,
                                                  typename Queue<P>::item* queue,
@@ -382,16 +502,16 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int i, typena
     using real = typename P::real;
     using pos4 = typename P::pos4;
     constexpr int kQ = Queue<P>::kSlots;
-    const int cnt = a.nn[i];
     const unsigned nlast = (unsigned)(a.n - 1);  // entries are always < n; the clamp only guards memory
-    const int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
     int nq = 0;
     for (int m = 0; m < cnt; m += 4) {
         unsigned e[4];
         pos4 pj[4];
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            e[k] = (m + k < cnt) ? (unsigned)__ldcs(col + (size_t)(m + k) * 32) : 0u;
+            e[k] = (m + k < cnt) ? (unsigned)(m + k < staged ? rows[(m + k) * 32 + (threadIdx.x & 31)]
+                                                             : __ldcs(col + (size_t)(m + k) * 32))
+                                 : 0u;
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (m + k < cnt) pj[k] = ld_pos4(pc + min(e[k] & (unsigned)kIndexMask, nlast));
@@ -415,6 +535,67 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int i, typena
     for (int k = 0; k < nk; k++) {
         const auto d = queue[k * kBlock + threadIdx.x];
         acc.template force<kEnergy>(a, d.x, d.y, d.z, d.w);
+    }
+}
+
+// Mixed-form counterpart of forces_from_list, in one pass: each entry's
+// pair term is evaluated as soon as its distance test passes.  Here the
+// shared-memory queue and the shift table cost more L1 data-pipe
+// wavefronts than the divergence they save, so the shift
+// -d w = (1 - k) w of each component (k the 2-bit code) is computed from
+// the code, and the staged rows and the rest of the column run as two loops
+// (no per-entry choice of source).  x and y travel as one packed pair.
+__device__ __forceinline__ float small_int_to_float(unsigned k) {  // exact for k < 2^22
+    return __uint_as_float(0x4B400000u | k) - 12582912.0f;
+}
+template <bool kEnergy>
+__device__ __forceinline__ void forces_mixed(const Args<Mixed>& a, int cnt, const int* col, const int* rows,
+                                             int staged, float qx, float qy, float qz,
+                                             const float4* __restrict__ pc, AccMixed& acc) {
+    const unsigned nlast = (unsigned)(a.n - 1);  // entries are always < n; the clamp only guards memory
+    const int lane = threadIdx.x & 31;
+    const F2 qxy = f2(qx, qy);
+    const F2 wxy = f2(a.wf[0], a.wf[1]);
+    const F2 nwxy = f2(-a.wf[0], -a.wf[1]);
+    const float wz = a.wf[2];
+    const float rc2 = a.rc2f;
+    auto pair = [&](unsigned e, const float4& pj) {
+        const unsigned c = e >> kCodeShift;
+        const F2 kxy = f2(small_int_to_float(c & 3u), small_int_to_float((c >> 2) & 3u));
+        const F2 sxy = f2_fma(kxy, nwxy, wxy);  // (1 - k) w, exact
+        const float sz = fmaf(small_int_to_float(c >> 4), -wz, wz);
+        const F2 dxy = f2_add(f2_sub(qxy, f2(pj.x, pj.y)), sxy);
+        const float dz = (qz - pj.z) + sz;
+        float sx, sy;
+        f2_get(f2_mul(dxy, dxy), sx, sy);
+        const float rr = fmaf(dz, dz, sx + sy);
+        if (rr < rc2) acc.template force<kEnergy>(a, dxy, dz, rr);
+    };
+    const int ns = min(cnt, staged);  // staged is a multiple of 4 or the capacity
+    int m = 0;
+    for (; m < ns; m += 4) {
+        unsigned e[4];
+        float4 pj[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) e[k] = (unsigned)rows[(m + k) * 32 + lane];  // rows past ns are unused
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (m + k < ns) pj[k] = __ldg(pc + min(e[k] & (unsigned)kIndexMask, nlast));
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (m + k < ns) pair(e[k], pj[k]);
+    }
+    for (m = ns; m < cnt; m += 4) {
+        unsigned e[4];
+        float4 pj[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) e[k] = (m + k < cnt) ? (unsigned)__ldcs(col + (size_t)(m + k) * 32) : 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (m + k < cnt) pj[k] = __ldg(pc + min(e[k] & (unsigned)kIndexMask, nlast));
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (m + k < cnt) pair(e[k], pj[k]);
     }
 }
 
@@ -442,7 +623,7 @@ __device__ __forceinline__ void forces_from_cells(const Args<P>& a, int i, typen
             for (int dx = -1; dx <= 1; dx++) {
                 int x = wrap_add(cx, dx, a.G[0]);
                 real sx = -(real)dx * wx;
-                int c2 = linear_cell(x, y, z, a.G);
+                int c2 = cell_index(x, y, z, a.G);
                 int beg = a.cell_start[c2], end = min(a.cell_start[c2 + 1], (int)a.n);
                 for (int t = beg; t < end; t++) {
                     float4 cj = __ldg(a.cand + t);
@@ -580,7 +761,7 @@ __global__ void __launch_bounds__(kBlock) k_bin(Args<P> a, int guard) {
     a.cell[i] = pack_cell(cc[0], cc[1], cc[2]);
     typename P::pos4* pc = C->parity ? a.pB : a.pA;
     pc[i] = make_pos4(pair_coord(pb[0], o[0]), pair_coord(pb[1], o[1]), pair_coord(pb[2], o[2]), 0);
-    a.rank[i] = atomicAdd(&a.count[linear_cell(cc[0], cc[1], cc[2], a.G)], 1);
+    a.rank[i] = atomicAdd(&a.count[cell_index(cc[0], cc[1], cc[2], a.G)], 1);
 }
 
 // Exclusive scan of the cell counts, phase 1: per-tile totals.
@@ -686,7 +867,7 @@ template <class P>
 __global__ void __launch_bounds__(kBlock) k_scatter(Args<P> a, int guard) {
     if (guard && !a.ctr->rebuild_flag) return;
     for (int64_t t = gtid(); t < a.n; t += (int64_t)gridDim.x * blockDim.x) {
-        int slot = a.cell_start[linear_of_packed(a.cell[t], a.G)] + a.rank[t];
+        int slot = a.cell_start[cell_index_of_packed(a.cell[t], a.G)] + a.rank[t];
         if (slot >= 0 && slot < a.n) a.order[slot] = (int)t;
         else atomicOr(&a.ctr->error, kErrUnstable);
     }
@@ -771,81 +952,67 @@ __device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int 
 }
 
 // Neighbour-list build (Sec. 3.4): for the atom in cell-ordered slot s, scan
-// the 27 cells around its cell -- as 9 rows of 3 cells, contiguous in cell
-// order unless the row wraps -- and record every j != i with r < r_n in its
+// the 27 cells around its cell and record every j != i with r < r_n in its
 // column together with the cell-offset code.  The decision is the exact
-// FP64 criterion; FP32 coordinates settle every candidate outside a narrow
-// band around r_n^2 and the FP64 test the rest.
+// FP64 criterion: FP32 coordinates settle every candidate outside a narrow
+// band around r_n^2, the FP64 test the rest.  The three cells of one
+// (c_y, c_z) row sit at base + c_x * stride in the pencil order, so each row
+// costs one index computation and the six range bounds are read together.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
     __shared__ int shm[kBlock / 32];
     __shared__ double shs[kBlock / 32];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
-    int64_t s = gtid();
+    const int64_t s = gtid();
     int m = 0;
     if (s < a.n) {
-        float4 ci = a.cand[s];
-        int i = __float_as_int(ci.w);
+        const float4 ci = a.cand[s];
+        const int i = __float_as_int(ci.w);
         int cx, cy, cz;
         unpack_cell(a.cell[i], cx, cy, cz);
         int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
-        const float qxm = ci.x + a.wf[0], qxp = ci.x - a.wf[0];  // x seen from cells x-1 and x+1
-        const bool inner = cx >= 1 && cx <= a.G[0] - 2;
-        const int xm = wrap_add(cx, -1, a.G[0]), xp = wrap_add(cx, 1, a.G[0]);
+        const int cap = a.cap, n = (int)a.n, self = (int)s;
+        const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
+        const int xs[3] = {wrap_add(cx, -1, a.G[0]), cx, wrap_add(cx, 1, a.G[0])};
+        const float qxs[3] = {ci.x + a.wf[0], ci.x, ci.x - a.wf[0]};  // x seen from cells x-1, x, x+1
         for (int dz = -1; dz <= 1; dz++) {
-            int z = wrap_add(cz, dz, a.G[2]);
-            float qz = ci.z - (float)dz * a.wf[2];
+            const int z = wrap_add(cz, dz, a.G[2]);
+            const float qz = ci.z - (float)dz * a.wf[2];
             for (int dy = -1; dy <= 1; dy++) {
-                int y = wrap_add(cy, dy, a.G[1]);
-                float qy = ci.y - (float)dy * a.wf[1];
-                unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
-                int row = (z * a.G[1] + y) * a.G[0];
-                // cells x-1, x, x+1 of this row: [r0, r1), [r1, r2), [r2, r3)
-                // when contiguous, else three separate ranges
-                int r0, r1, r2, r3, e0, f0;
-                if (inner) {
-                    r0 = a.cell_start[row + cx - 1];
-                    r1 = a.cell_start[row + cx];
-                    r2 = a.cell_start[row + cx + 1];
-                    r3 = a.cell_start[row + cx + 2];
-                    e0 = r1;
-                    f0 = r2;
-                } else {
-                    r0 = a.cell_start[row + xm];
-                    e0 = a.cell_start[row + xm + 1];
-                    r1 = a.cell_start[row + cx];
-                    r2 = a.cell_start[row + cx + 1];
-                    f0 = a.cell_start[row + xp];
-                    r3 = a.cell_start[row + xp + 1];
+                const int y = wrap_add(cy, dy, a.G[1]);
+                const float qy = ci.y - (float)dy * a.wf[1];
+                const unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
+                const PencilRow pr = pencil_row(y, z, a.G);
+                int lo[3], hi[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const int c = pr.base + xs[k] * pr.stride;
+                    lo[k] = a.cell_start[c];
+                    hi[k] = min(a.cell_start[c + 1], n);
                 }
-                // pieces: [r0, e0) is x-1, [r1, r2) is x, [f0, r3) is x+1
-                for (int piece = 0; piece < 3; piece++) {
-                    int lo = piece == 0 ? r0 : (piece == 1 ? r1 : f0);
-                    int hi = piece == 0 ? e0 : (piece == 1 ? r2 : r3);
-                    hi = min(hi, (int)a.n);
-                    const float qx = piece == 0 ? qxm : (piece == 1 ? ci.x : qxp);
-                    const unsigned code = (unsigned)piece | code_yz;
-                    for (int t = lo; t < hi; t++) {
-                        if (t == s) continue;
-                        float4 pj = __ldg(a.cand + t);
-                        float ex = qx - pj.x;
-                        float ey = qy - pj.y;
-                        float ez = qz - pj.z;
-                        float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        int j = __float_as_int(pj.w);
-                        bool take = rr < a.rn2_lo;
-                        if (!take && rr < a.rn2_hi) take = within_rn_fp64(a, i, j, piece - 1, dy, dz);
-                        if (take) {
-                            if (m < a.cap) col[(size_t)m * 32] = j | (int)(code << kCodeShift);
-                            m++;
-                        }
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    const float qx = qxs[k];
+                    const int code = (int)(((unsigned)k | code_yz) << kCodeShift);
+                    for (int t = lo[k]; t < hi[k]; t++) {
+                        const float4 pj = __ldg(a.cand + t);
+                        const float ex = qx - pj.x;
+                        const float ey = qy - pj.y;
+                        const float ez = qz - pj.z;
+                        const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        const int j = __float_as_int(pj.w);
+                        bool take = rr < lo2;
+                        if (!take && rr < hi2) take = within_rn_fp64(a, i, j, k - 1, dy, dz);
+                        take = take && t != self;
+                        if (take && m < cap) col[(size_t)m * 32] = j | code;
+                        m += take ? 1 : 0;
                     }
                 }
             }
         }
-        a.nn[i] = m < a.cap ? m : a.cap;
-        if (m > a.cap) {
+        a.nn[i] = m < cap ? m : cap;
+        if (m > cap) {
             atomicOr(&C->error, kErrOverflow);
             atomicMax(&C->need_cap, m);
         }
@@ -949,16 +1116,47 @@ __global__ void __launch_bounds__(kBlock) k_kickdrift(Args<P> a, long long nstep
 // every other step, carries no energy accumulators.  The last block
 // advances the counters and, in a graph, sets the next conditional rebuild.
 template <class P, bool kCells, bool kFinal>
-__global__ void __launch_bounds__(kBlock) k_step(Args<P> a, int mode, cudaGraphConditionalHandle next,
+__global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, int mode, cudaGraphConditionalHandle next,
                                                  int has_next) {
     using real = typename P::real;
     using vel = typename P::vel;
     using pos4 = typename P::pos4;
     __shared__ double shs[kBlock / 32];
-    __shared__ pos4 s_shift[64];
-    __shared__ typename Queue<P>::item s_queue[kCells ? 1 : Queue<P>::kSlots * kBlock];
+    constexpr bool kTable = P::kFp64 && !kCells;  // shift table and pair queue (FP64 list form)
+    __shared__ pos4 s_shift[kTable ? 64 : 1];
+    __shared__ typename Queue<P>::item s_queue[kTable ? Queue<P>::kSlots * kBlock : 1];
+    __shared__ __align__(16) int s_rows[kCells ? 4 : kStageRows * kBlock];
     Counters* C = a.ctr;
-    if constexpr (!kCells) fill_shift_table<P>(a, s_shift);
+    if constexpr (kTable) fill_shift_table<P>(a, s_shift);
+    // Requests that do not depend on the counters go out first, so their
+    // latency overlaps the counter read: the first rows of the warp's
+    // neighbour column block (copied to shared memory; rows below the
+    // capacity always exist, unused ones are ignored) and the neighbour
+    // count.  The pair coordinate q_i comes from the current pair buffer
+    // (bit-identical to pb + o rounded, which wrote it); pb and o are read
+    // after the force loop, where they are needed.
+    const int64_t i = gtid();
+    const bool in = i < a.n;
+    int cnt = 0, staged = 0;
+    const int* col = nullptr;
+    int* rows = s_rows + (threadIdx.x >> 5) * (kStageRows * 32);
+    if constexpr (!kCells) {
+        if ((i & ~(int64_t)31) < a.n) {  // the warp's column block exists
+            staged = min(a.cap, kStageRows);
+            const int* blk = a.nbr + (size_t)(i >> 5) * (size_t)a.cap * 32;
+            for (int c = threadIdx.x & 31; c < staged * 8; c += 32) cp_async16(rows + 4 * c, blk + 4 * c);
+        }
+    }
+    if (in) {
+        if constexpr (!kCells) {
+            cnt = a.nn[i];
+            col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
+        }
+    }
+    if constexpr (!kCells) {
+        cp_async_wait_all();
+        __syncwarp();
+    }
     const View vw = load_view(C);  // also orders the table fill before its use
     const int err = vw.err;
     const long long left = vw.left;
@@ -970,24 +1168,28 @@ __global__ void __launch_bounds__(kBlock) k_step(Args<P> a, int mode, cudaGraphC
     const bool energy = init || last;
     const pos4* pc = par ? a.pB : a.pA;
     pos4* pn = par ? a.pA : a.pB;
-    int64_t i = gtid();
     bool far = false, close = false;
     double ke = 0.0, pe = 0.0, vir = 0.0;
-    if (active && i < a.n) {
-        real pbx = a.pbx[i], pby = a.pby[i], pbz = a.pbz[i];
-        double ox = a.ox[i], oy = a.oy[i], oz = a.oz[i];
-        real qx = pair_coord(pbx, ox), qy = pair_coord(pby, oy), qz = pair_coord(pbz, oz);
+    if (active && in) {
+        const pos4 qi = ld_pos4(pc + i);
+        const real qx = qi.x, qy = qi.y, qz = qi.z;
         typename AccOf<P>::type acc;
         if (kFinal && energy) {
             if constexpr (kCells) forces_from_cells<P, kFinal>(a, (int)i, qx, qy, qz, pc, acc);
-            else forces_from_list<P, kFinal>(a, (int)i, qx, qy, qz, pc, s_shift, s_queue, acc);
+            else if constexpr (P::kFp64)
+                forces_from_list<P, kFinal>(a, cnt, col, rows, staged, qx, qy, qz, pc, s_shift, s_queue, acc);
+            else forces_mixed<kFinal>(a, cnt, col, rows, staged, qx, qy, qz, pc, acc);
         } else {
             if constexpr (kCells) forces_from_cells<P, false>(a, (int)i, qx, qy, qz, pc, acc);
-            else forces_from_list<P, false>(a, (int)i, qx, qy, qz, pc, s_shift, s_queue, acc);
+            else if constexpr (P::kFp64)
+                forces_from_list<P, false>(a, cnt, col, rows, staged, qx, qy, qz, pc, s_shift, s_queue, acc);
+            else forces_mixed<false>(a, cnt, col, rows, staged, qx, qy, qz, pc, acc);
         }
         close = acc.close != 0;
         real fx = acc.force_x(), fy = acc.force_y(), fz = acc.force_z();
         vel vx = a.vx[i], vy = a.vy[i], vz = a.vz[i];
+        const real pbx = a.pbx[i], pby = a.pby[i], pbz = a.pbz[i];
+        double ox = a.ox[i], oy = a.oy[i], oz = a.oz[i];
         if (!init) {
             vx = kick(a, vx, fx);
             vy = kick(a, vy, fy);
