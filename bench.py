@@ -42,7 +42,7 @@ L2_BYTES = 129 * 2 ** 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="wca_fcc64_n1m")
@@ -95,17 +95,24 @@ def kernel_source_hash():
 
 
 def ncu_traffic(workload, precision):
-    """Per-launch DRAM bytes of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    """Per-launch DRAM bytes (read + write) of the step kernel from the
+    committed ncu summary, if that summary was taken on the current kernel
+    source (its `kernel_source` line matches); else None."""
+    p = os.path.join(ROOT, "profiles", "k_step_%s_%s.md" % (workload, precision))
     if not os.path.exists(p):
         return None
+    fields = {}
     with open(p) as fh:
-        d = json.load(fh)
-    e = d.get("%s/%s" % (workload, precision))
-    if not e or e.get("kernel_source") != kernel_source_hash():
+        for line in fh:
+            if " = " in line and not line.startswith("|"):
+                k, v = line.strip().split(" = ", 1)
+                fields[k] = v
+    if fields.get("kernel_source") != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 class Clocks:
@@ -189,7 +196,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(pos, vel, L, cfg, seconds=12.0):
+def cpu_baseline(pos, vel, L, cfg, seconds=15.0):
     """The oracle as it stands, single-threaded, on a bounded sample."""
     import oracle
     n = pos.shape[0]
