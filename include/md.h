@@ -256,6 +256,104 @@ int md_selftest(int64_t n, int64_t failures[4]);
 int md_forces_noalloc(const double box[3], int64_t n, double rc, double ushift, const double* pos,
                       double* f, double* pe_vir, void* stream);
 
+/* ---- ensembles: many independent simulations in one launch -------------
+ * The paper runs one simulation at a time.  An ensemble holds many
+ * independent replicas of the mixed form (each its own box, N, r_c, skin,
+ * dt and state) in one device arena, and md_ensemble_run advances any
+ * subset of them in a single kernel launch: each replica is taken by one
+ * thread block, which runs Sec. 3.1's steps (a)-(e) for it exactly as
+ * md_set_state/md_step do -- binning, neighbour-list rebuilds at skin/2,
+ * reorders every reorder_interval steps, forces, the velocity-Verlet
+ * update.  Replicas share nothing, so a replica's trajectory does not
+ * depend on what else runs: positions and velocities are bitwise those of
+ * md_step from the same state, and KE, PE and W are summed in a fixed
+ * order over 32-atom chunks, the same numbers whatever the launch shape.
+ *
+ * Memory: md_ensemble_create reserves arena_bytes of device memory once;
+ * md_ensemble_add carves a replica's arrays out of it (MD_ENOMEM when they
+ * do not fit: the caller's admission signal) and md_ensemble_remove gives
+ * them back.  Replica ids are small non-negative integers, reused after
+ * removal.  One ensemble is not thread-safe; calls are ordered on its
+ * stream.  Errors of a replica (overflow of its neighbour capacity, an
+ * unstable state) stop that replica only; md_ensemble_status reports them.
+ */
+typedef struct md_replica_desc {
+    double box[3];             /* region edges, each at least 3 (rc + skin)   */
+    int64_t n;                 /* atoms, 1 .. 2^26 - 1                         */
+    double rc, skin, dt;       /* cutoff, shell, time step (Sec. 3.1)          */
+    double ushift;             /* added to u below rc; NaN: +1 for the WCA rc  */
+    int32_t reorder_interval;  /* reorder into cell order every this many
+                                  steps at the next rebuild (Sec. 5.5); 0 never */
+    int32_t nbr_capacity;      /* neighbour slots per atom; 0: from density    */
+    int64_t reserved[4];       /* must be zero                                 */
+} md_replica_desc;
+
+typedef struct md_ensemble md_ensemble;
+
+/* Creates an ensemble with an arena of arena_bytes on device (-1: current)
+ * and up to max_replicas replica ids.  stream: cudaStream_t for all work
+ * (NULL: the ensemble creates its own). */
+int md_ensemble_create(int64_t arena_bytes, int32_t max_replicas, int32_t device, void* stream,
+                       md_ensemble** out);
+
+/* Adds a replica with positions and velocities (host, n x 3 doubles each,
+ * copied before return).  Its state is loaded (wrapped, binned, listed,
+ * forces computed) at the start of the next md_ensemble_run that includes
+ * it.  *id receives its id.  MD_EINVAL on a bad description, MD_ENOMEM when
+ * the arena or the id table is full. */
+int md_ensemble_add(md_ensemble* e, const md_replica_desc* d, const double* pos, const double* vel,
+                    int32_t* id);
+
+/* Frees a replica's arena space and id (waits for queued work first). */
+int md_ensemble_remove(md_ensemble* e, int32_t id);
+
+/* Advances replicas ids[0..count) by nsteps[k] >= 0 steps each in one
+ * launch (asynchronous; replicas added since their last run are loaded
+ * first, so nsteps 0 only loads them).  An id may appear once per call. */
+int md_ensemble_run(md_ensemble* e, int32_t count, const int32_t* ids, const int64_t* nsteps);
+
+/* Waits for the ensemble's stream. */
+int md_ensemble_sync(md_ensemble* e);
+
+/* MD_OK, or the error that stopped the replica (MD_EOVERFLOW, MD_EUNSTABLE). */
+int md_ensemble_status(md_ensemble* e, int32_t id);
+
+/* Thermodynamic state of a replica after its last run (as md_measure). */
+int md_ensemble_measure(md_ensemble* e, int32_t id, md_measure_t* out);
+
+/* Positions (wrapped) and velocities of a replica in its user order
+ * (host, n x 3 doubles each). */
+int md_ensemble_get_state(md_ensemble* e, int32_t id, double* pos, double* vel);
+
+/* Start and end of each listed replica's work in the last run that
+ * included it, in ms after that run's launch began on the device (device
+ * clock); -1 for a replica not yet run. */
+int md_ensemble_times(md_ensemble* e, int32_t count, const int32_t* ids, double* start_ms, double* end_ms);
+
+/* Launch shape for md_ensemble_run: threads per block (a multiple of 32,
+ * 64 .. 1024) and blocks (0: as many as fit on the device at once).
+ * block 0 restores the default (256). */
+int md_ensemble_set_shape(md_ensemble* e, int32_t block, int32_t grid);
+
+/* Autotuner: runs ids for probe_steps steps under each candidate launch
+ * shape (these are real steps: the replicas advance by
+ * probe_steps x number of candidates), keeps the fastest shape and returns
+ * it in *block, *grid (either may be NULL). */
+int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int64_t probe_steps,
+                         int32_t* block, int32_t* grid);
+
+/* Arena bytes a replica of this description needs (0 on a bad one), and
+ * the largest free arena block right now. */
+int64_t md_ensemble_replica_bytes(const md_replica_desc* d);
+int64_t md_ensemble_free_bytes(const md_ensemble* e);
+
+/* Frees everything.  NULL is a no-op. */
+void md_ensemble_destroy(md_ensemble* e);
+
+/* Message for the ensemble's last failure ("" if none); e may be NULL for
+ * failures of md_ensemble_create. */
+const char* md_ensemble_last_error(const md_ensemble* e);
+
 /* Static description of an error code. */
 const char* md_strerror(int code);
 

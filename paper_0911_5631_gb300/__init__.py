@@ -108,6 +108,20 @@ class md_kernel_stats_t(C.Structure):
     ]
 
 
+class md_replica_desc(C.Structure):
+    _fields_ = [
+        ("box", C.c_double * 3),
+        ("n", C.c_int64),
+        ("rc", C.c_double),
+        ("skin", C.c_double),
+        ("dt", C.c_double),
+        ("ushift", C.c_double),
+        ("reorder_interval", C.c_int32),
+        ("nbr_capacity", C.c_int32),
+        ("reserved", C.c_int64 * 4),
+    ]
+
+
 # (name, restype, argtypes) of every exported function, in header order.
 _H = C.c_void_p
 _D3 = C.POINTER(C.c_double)
@@ -136,6 +150,23 @@ SIGNATURES = [
     ("md_selftest", C.c_int, [C.c_int64, C.POINTER(C.c_int64)]),
     ("md_forces_noalloc", C.c_int, [_D3, C.c_int64, C.c_double, C.c_double, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
+    ("md_ensemble_create", C.c_int, [C.c_int64, C.c_int32, C.c_int32, C.c_void_p, C.POINTER(_H)]),
+    ("md_ensemble_add", C.c_int, [_H, C.POINTER(md_replica_desc), C.c_void_p, C.c_void_p,
+                                  C.POINTER(C.c_int32)]),
+    ("md_ensemble_remove", C.c_int, [_H, C.c_int32]),
+    ("md_ensemble_run", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("md_ensemble_sync", C.c_int, [_H]),
+    ("md_ensemble_status", C.c_int, [_H, C.c_int32]),
+    ("md_ensemble_measure", C.c_int, [_H, C.c_int32, C.POINTER(md_measure_t)]),
+    ("md_ensemble_get_state", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_void_p]),
+    ("md_ensemble_times", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("md_ensemble_set_shape", C.c_int, [_H, C.c_int32, C.c_int32]),
+    ("md_ensemble_autotune", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32)]),
+    ("md_ensemble_replica_bytes", C.c_int64, [C.POINTER(md_replica_desc)]),
+    ("md_ensemble_free_bytes", C.c_int64, [_H]),
+    ("md_ensemble_destroy", None, [_H]),
+    ("md_ensemble_last_error", C.c_char_p, [_H]),
     ("md_strerror", C.c_char_p, [C.c_int]),
 ]
 
@@ -391,6 +422,121 @@ class Simulation:
         if getattr(self, "h", None):
             md_destroy(self.h)
             self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---- ensembles -------------------------------------------------------------
+
+def _ens_check(code, e):
+    if code != MD_OK:
+        raise MDError(code, lib().md_ensemble_last_error(e).decode())
+    return code
+
+
+def replica_desc(box, n, rc=WCA_RC, skin=0.4, dt=0.005, reorder_interval=100, nbr_capacity=0, ushift=None):
+    d = md_replica_desc()
+    b = np.broadcast_to(np.asarray(box, dtype=np.float64), (3,))
+    for k in range(3):
+        d.box[k] = float(b[k])
+    d.n = int(n)
+    d.rc, d.skin, d.dt = float(rc), float(skin), float(dt)
+    d.ushift = float("nan") if ushift is None else float(ushift)
+    d.reorder_interval = int(reorder_interval)
+    d.nbr_capacity = int(nbr_capacity)
+    return d
+
+
+def md_ensemble_replica_bytes(d: md_replica_desc) -> int:
+    return int(lib().md_ensemble_replica_bytes(C.byref(d)))
+
+
+class Ensemble:
+    """Many independent mixed-form replicas in one device arena, advanced
+    together by one launch per ``run`` (md_ensemble_* in md.h)."""
+
+    def __init__(self, arena_bytes, max_replicas=4096, device=-1, stream=None):
+        h = _H()
+        code = lib().md_ensemble_create(int(arena_bytes), int(max_replicas), int(device), stream, C.byref(h))
+        if code != MD_OK:
+            raise MDError(code, lib().md_ensemble_last_error(None).decode())
+        self.e = h
+        self.n = {}
+
+    def add(self, pos, vel, box, rc=WCA_RC, skin=0.4, dt=0.005, reorder_interval=100, nbr_capacity=0,
+            ushift=None) -> int:
+        n = np.asarray(pos).shape[0]
+        d = replica_desc(box, n, rc, skin, dt, reorder_interval, nbr_capacity, ushift)
+        p = _host3(pos, n)
+        v = _host3(vel, n)
+        rid = C.c_int32()
+        _ens_check(lib().md_ensemble_add(self.e, C.byref(d), p.ctypes.data, v.ctypes.data, C.byref(rid)), self.e)
+        self.n[rid.value] = n
+        return rid.value
+
+    def remove(self, rid):
+        _ens_check(lib().md_ensemble_remove(self.e, int(rid)), self.e)
+        self.n.pop(int(rid), None)
+
+    def run(self, ids, nsteps):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        st = np.ascontiguousarray(np.broadcast_to(np.asarray(nsteps, dtype=np.int64), ids.shape))
+        _ens_check(lib().md_ensemble_run(self.e, int(ids.size), ids.ctypes.data, st.ctypes.data), self.e)
+
+    def sync(self):
+        _ens_check(lib().md_ensemble_sync(self.e), self.e)
+
+    def status(self, rid) -> int:
+        return int(lib().md_ensemble_status(self.e, int(rid)))
+
+    def measure(self, rid) -> dict:
+        m = md_measure_t()
+        _ens_check(lib().md_ensemble_measure(self.e, int(rid), C.byref(m)), self.e)
+        return _struct_dict(m)
+
+    def get_state(self, rid):
+        n = self.n[int(rid)]
+        pos = np.empty((n, 3))
+        vel = np.empty((n, 3))
+        _ens_check(lib().md_ensemble_get_state(self.e, int(rid), pos.ctypes.data, vel.ctypes.data), self.e)
+        return pos, vel
+
+    def times(self, ids):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        t0 = np.empty(ids.size)
+        t1 = np.empty(ids.size)
+        _ens_check(lib().md_ensemble_times(self.e, int(ids.size), ids.ctypes.data, t0.ctypes.data, t1.ctypes.data),
+                   self.e)
+        return t0, t1
+
+    def set_shape(self, block=0, grid=0):
+        _ens_check(lib().md_ensemble_set_shape(self.e, int(block), int(grid)), self.e)
+
+    def autotune(self, ids, probe_steps=20):
+        ids = np.ascontiguousarray(ids, dtype=np.int32)
+        b = C.c_int32()
+        g = C.c_int32()
+        _ens_check(lib().md_ensemble_autotune(self.e, int(ids.size), ids.ctypes.data, int(probe_steps), C.byref(b),
+                                              C.byref(g)), self.e)
+        return b.value, g.value
+
+    def free_bytes(self) -> int:
+        return int(lib().md_ensemble_free_bytes(self.e))
+
+    def close(self):
+        if getattr(self, "e", None):
+            lib().md_ensemble_destroy(self.e)
+            self.e = None
 
     def __enter__(self):
         return self

@@ -18,8 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmd.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-UNITS = ["md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_api.cu", "md_noalloc.cu"]
-HEADERS = ["md_common.cuh", "md_kernels.cuh", "md_table.h"]
+UNITS = ["md_kernels_mixed.cu", "md_kernels_fp64.cu", "md_api.cu", "md_noalloc.cu", "md_ensemble.cu"]
+HEADERS = ["md_common.cuh", "md_kernels.cuh", "md_table.h", "md_host.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -63,6 +63,15 @@ struct Counters {
     double ke, pe, virial;
 };
 
+// One job of an ensemble launch: replica `rep` (index into the Args array);
+// load its state first when `init`; then advance it `nsteps` steps.
+struct EnsJob {
+    int rep;
+    int init;
+    long long nsteps;
+    unsigned long long t_start, t_end;  // device clock (ns) around the job's work
+};
+
 // Precision forms.  real: pair arithmetic, build offsets and saved forces;
 // vel: velocity storage; pos4: gathered coordinates (x, y, z, payload).
 struct Mixed {
@@ -80,7 +89,7 @@ struct F64 {
 
 // Everything the kernels need, passed by value.  Device pointers only.
 template <class P>
-struct Args {
+struct alignas(16) Args {
     using real = typename P::real;
     using vel = typename P::vel;
     using pos4 = typename P::pos4;

@@ -651,10 +651,8 @@ __device__ __forceinline__ void forces_from_cells(const Args<P>& a, int i, typen
 // t = x + L/2, c = floor(t G / L), faces folded back into range) and splits
 // the offset from the cell centre into (pb, o).  Storage order = user order.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_set_state(Args<P> a) {
+__device__ __forceinline__ void set_state_item(const Args<P>& a, int64_t i) {
     using real = typename P::real;
-    int64_t i = gtid();
-    if (i >= a.n) return;
     int c[3];
     real pb[3];
     double o[3];
@@ -697,6 +695,14 @@ __global__ void __launch_bounds__(kBlock) k_set_state(Args<P> a) {
     a.pA[i] = make_pos4(pair_coord(pb[0], o[0]), pair_coord(pb[1], o[1]), pair_coord(pb[2], o[2]), 0);
 }
 
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_set_state(Args<P> a) {
+    using real = typename P::real;
+    int64_t i = gtid();
+    if (i >= a.n) return;
+    set_state_item<P>(a, i);
+}
+
 // Counters for a freshly loaded state: a rebuild with reorder is pending.
 template <class P>
 __global__ void k_reset_counters(Counters* C) {
@@ -728,12 +734,9 @@ __global__ void k_clear_overflow(Counters* C) {
 // is an integer operation on the cell coordinate).  Refreshes the pair
 // coordinate and counts the atoms of each cell.
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_bin(Args<P> a, int guard) {
+__device__ __forceinline__ void bin_item(const Args<P>& a, int64_t i) {
     using real = typename P::real;
     Counters* C = a.ctr;
-    if (guard && !C->rebuild_flag) return;
-    int64_t i = gtid();
-    if (i >= a.n) return;
     int cc[3];
     unpack_cell(a.cell[i], cc[0], cc[1], cc[2]);
     real* pbp[3] = {a.pbx, a.pby, a.pbz};
@@ -762,6 +765,16 @@ __global__ void __launch_bounds__(kBlock) k_bin(Args<P> a, int guard) {
     typename P::pos4* pc = C->parity ? a.pB : a.pA;
     pc[i] = make_pos4(pair_coord(pb[0], o[0]), pair_coord(pb[1], o[1]), pair_coord(pb[2], o[2]), 0);
     a.rank[i] = atomicAdd(&a.count[cell_index(cc[0], cc[1], cc[2], a.G)], 1);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_bin(Args<P> a, int guard) {
+    using real = typename P::real;
+    Counters* C = a.ctr;
+    if (guard && !C->rebuild_flag) return;
+    int64_t i = gtid();
+    if (i >= a.n) return;
+    bin_item<P>(a, i);
 }
 
 // Exclusive scan of the cell counts, phase 1: per-tile totals.
@@ -864,23 +877,23 @@ __global__ void __launch_bounds__(kBlock) k_scan_apply(Args<P> a, int guard) {
 // Places each atom at cell_start[cell] + rank (the cell's arrival order)
 // and clears the counts for the next binning.
 template <class P>
+__device__ __forceinline__ void scatter_item(const Args<P>& a, int64_t t) {
+    int slot = a.cell_start[cell_index_of_packed(a.cell[t], a.G)] + a.rank[t];
+    if (slot >= 0 && slot < a.n) a.order[slot] = (int)t;
+    else atomicOr(&a.ctr->error, kErrUnstable);
+}
+
+template <class P>
 __global__ void __launch_bounds__(kBlock) k_scatter(Args<P> a, int guard) {
     if (guard && !a.ctr->rebuild_flag) return;
-    for (int64_t t = gtid(); t < a.n; t += (int64_t)gridDim.x * blockDim.x) {
-        int slot = a.cell_start[cell_index_of_packed(a.cell[t], a.G)] + a.rank[t];
-        if (slot >= 0 && slot < a.n) a.order[slot] = (int)t;
-        else atomicOr(&a.ctr->error, kErrUnstable);
-    }
+    for (int64_t t = gtid(); t < a.n; t += (int64_t)gridDim.x * blockDim.x) scatter_item<P>(a, t);
     // counts are no longer needed once cell_start is known
     for (int64_t t = gtid(); t < a.ncells; t += (int64_t)gridDim.x * blockDim.x) a.count[t] = 0;
 }
 
 // Makes the order inside each cell deterministic (ascending storage index).
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_cellsort(Args<P> a, int guard) {
-    if (guard && !a.ctr->rebuild_flag) return;
-    int64_t c = gtid();
-    if (c >= a.ncells) return;
+__device__ __forceinline__ void cellsort_item(const Args<P>& a, int64_t c) {
     int beg = a.cell_start[c], end = a.cell_start[c + 1];
     for (int s = beg + 1; s < end; s++) {
         int key = a.order[s];
@@ -893,15 +906,20 @@ __global__ void __launch_bounds__(kBlock) k_cellsort(Args<P> a, int guard) {
     }
 }
 
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_cellsort(Args<P> a, int guard) {
+    if (guard && !a.ctr->rebuild_flag) return;
+    int64_t c = gtid();
+    if (c >= a.ncells) return;
+    cellsort_item<P>(a, c);
+}
+
 // Writes the cell-ordered FP32 coordinate copy used by the neighbour search
 // and, when a reorder is due, the state permuted into cell order (Sec. 3.5).
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_gather(Args<P> a, int guard) {
+__device__ __forceinline__ void gather_item(const Args<P>& a, int64_t s) {
     using real = typename P::real;
     Counters* C = a.ctr;
-    if (guard && !C->rebuild_flag) return;
-    int64_t s = gtid();
-    if (s >= a.n) return;
     const int reorder = C->reorder_now;
     int i = a.order[s];
     real pbx = a.pbx[i], pby = a.pby[i], pbz = a.pbz[i];
@@ -917,15 +935,21 @@ __global__ void __launch_bounds__(kBlock) k_gather(Args<P> a, int guard) {
     }
 }
 
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_gather(Args<P> a, int guard) {
+    using real = typename P::real;
+    Counters* C = a.ctr;
+    if (guard && !C->rebuild_flag) return;
+    int64_t s = gtid();
+    if (s >= a.n) return;
+    gather_item<P>(a, s);
+}
+
 // Copies the permuted state back and rewrites the current pair buffer in
 // the new order (only when a reorder is due).
 template <class P>
-__global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
+__device__ __forceinline__ void commit_item(const Args<P>& a, int64_t s) {
     Counters* C = a.ctr;
-    if (guard && !C->rebuild_flag) return;
-    if (!C->reorder_now) return;
-    int64_t s = gtid();
-    if (s >= a.n) return;
     a.cell[s] = a.s_cell[s];
     a.perm[s] = a.s_perm[s];
     auto pbx = a.s_pbx[s], pby = a.s_pby[s], pbz = a.s_pbz[s];
@@ -935,6 +959,16 @@ __global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
     a.vx[s] = a.s_vx[s]; a.vy[s] = a.s_vy[s]; a.vz[s] = a.s_vz[s];
     typename P::pos4* pc = C->parity ? a.pB : a.pA;
     pc[s] = make_pos4(pair_coord(pbx, ox), pair_coord(pby, oy), pair_coord(pbz, oz), 0);
+}
+
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
+    Counters* C = a.ctr;
+    if (guard && !C->rebuild_flag) return;
+    if (!C->reorder_now) return;
+    int64_t s = gtid();
+    if (s >= a.n) return;
+    commit_item<P>(a, s);
 }
 
 // Exact FP64 neighbour criterion r^2 < r_n^2 on the cell-relative offsets
@@ -959,64 +993,69 @@ __device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int 
 // (c_y, c_z) row sit at base + c_x * stride in the pencil order, so each row
 // costs one index computation and the six range bounds are read together.
 template <class P>
+__device__ __forceinline__ int build_item(const Args<P>& a, int64_t s) {
+    Counters* C = a.ctr;
+    int m = 0;
+    const float4 ci = a.cand[s];
+    const int i = __float_as_int(ci.w);
+    int cx, cy, cz;
+    unpack_cell(a.cell[i], cx, cy, cz);
+    int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
+    const int cap = a.cap, n = (int)a.n, self = (int)s;
+    const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
+    const int xs[3] = {wrap_add(cx, -1, a.G[0]), cx, wrap_add(cx, 1, a.G[0])};
+    const float qxs[3] = {ci.x + a.wf[0], ci.x, ci.x - a.wf[0]};  // x seen from cells x-1, x, x+1
+    for (int dz = -1; dz <= 1; dz++) {
+        const int z = wrap_add(cz, dz, a.G[2]);
+        const float qz = ci.z - (float)dz * a.wf[2];
+        for (int dy = -1; dy <= 1; dy++) {
+            const int y = wrap_add(cy, dy, a.G[1]);
+            const float qy = ci.y - (float)dy * a.wf[1];
+            const unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
+            const PencilRow pr = pencil_row(y, z, a.G);
+            int lo[3], hi[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int c = pr.base + xs[k] * pr.stride;
+                lo[k] = a.cell_start[c];
+                hi[k] = min(a.cell_start[c + 1], n);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float qx = qxs[k];
+                const int code = (int)(((unsigned)k | code_yz) << kCodeShift);
+                for (int t = lo[k]; t < hi[k]; t++) {
+                    const float4 pj = __ldg(a.cand + t);
+                    const float ex = qx - pj.x;
+                    const float ey = qy - pj.y;
+                    const float ez = qz - pj.z;
+                    const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                    const int j = __float_as_int(pj.w);
+                    bool take = rr < lo2;
+                    if (!take && rr < hi2) take = within_rn_fp64(a, i, j, k - 1, dy, dz);
+                    take = take && t != self;
+                    if (take && m < cap) col[(size_t)m * 32] = j | code;
+                    m += take ? 1 : 0;
+                }
+            }
+        }
+    }
+    a.nn[i] = m < cap ? m : cap;
+    if (m > cap) {
+        atomicOr(&C->error, kErrOverflow);
+        atomicMax(&C->need_cap, m);
+    }
+    return m;
+}
+
+template <class P>
 __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
     __shared__ int shm[kBlock / 32];
     __shared__ double shs[kBlock / 32];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     const int64_t s = gtid();
-    int m = 0;
-    if (s < a.n) {
-        const float4 ci = a.cand[s];
-        const int i = __float_as_int(ci.w);
-        int cx, cy, cz;
-        unpack_cell(a.cell[i], cx, cy, cz);
-        int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
-        const int cap = a.cap, n = (int)a.n, self = (int)s;
-        const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
-        const int xs[3] = {wrap_add(cx, -1, a.G[0]), cx, wrap_add(cx, 1, a.G[0])};
-        const float qxs[3] = {ci.x + a.wf[0], ci.x, ci.x - a.wf[0]};  // x seen from cells x-1, x, x+1
-        for (int dz = -1; dz <= 1; dz++) {
-            const int z = wrap_add(cz, dz, a.G[2]);
-            const float qz = ci.z - (float)dz * a.wf[2];
-            for (int dy = -1; dy <= 1; dy++) {
-                const int y = wrap_add(cy, dy, a.G[1]);
-                const float qy = ci.y - (float)dy * a.wf[1];
-                const unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
-                const PencilRow pr = pencil_row(y, z, a.G);
-                int lo[3], hi[3];
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const int c = pr.base + xs[k] * pr.stride;
-                    lo[k] = a.cell_start[c];
-                    hi[k] = min(a.cell_start[c + 1], n);
-                }
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    const float qx = qxs[k];
-                    const int code = (int)(((unsigned)k | code_yz) << kCodeShift);
-                    for (int t = lo[k]; t < hi[k]; t++) {
-                        const float4 pj = __ldg(a.cand + t);
-                        const float ex = qx - pj.x;
-                        const float ey = qy - pj.y;
-                        const float ez = qz - pj.z;
-                        const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                        const int j = __float_as_int(pj.w);
-                        bool take = rr < lo2;
-                        if (!take && rr < hi2) take = within_rn_fp64(a, i, j, k - 1, dy, dz);
-                        take = take && t != self;
-                        if (take && m < cap) col[(size_t)m * 32] = j | code;
-                        m += take ? 1 : 0;
-                    }
-                }
-            }
-        }
-        a.nn[i] = m < cap ? m : cap;
-        if (m > cap) {
-            atomicOr(&C->error, kErrOverflow);
-            atomicMax(&C->need_cap, m);
-        }
-    }
+    const int m = s < a.n ? build_item<P>(a, s) : 0;
     int bm = block_max_int(m, shm);
     double bs = block_sum((double)m, shs);
     if (threadIdx.x == 0) {
@@ -1066,6 +1105,26 @@ __device__ __forceinline__ int decide_rebuild(Counters* C, int cell_list_only, i
 __device__ __forceinline__ float kick(const Args<Mixed>& a, float v, float f) { return fmaf(a.hf, f, v); }
 __device__ __forceinline__ double kick(const Args<F64>& a, double v, double f) { return fma(a.h, f, v); }
 
+// One atom of k_kickdrift; returns whether it has moved skin/2.
+template <class P>
+__device__ __forceinline__ bool kickdrift_item(const Args<P>& a, int64_t i, typename P::pos4* pc) {
+    using real = typename P::real;
+    using vel = typename P::vel;
+    vel vx = kick(a, a.vx[i], a.fx[i]);
+    vel vy = kick(a, a.vy[i], a.fy[i]);
+    vel vz = kick(a, a.vz[i], a.fz[i]);
+    double ox = drift(a.ox[i], vx, a.dt);
+    double oy = drift(a.oy[i], vy, a.dt);
+    double oz = drift(a.oz[i], vz, a.dt);
+    real px, py, pz;
+    real d2 = moved(a.pbx[i], ox, px) + moved(a.pby[i], oy, py) + moved(a.pbz[i], oz, pz);
+    a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
+    a.ox[i] = ox; a.oy[i] = oy; a.oz[i] = oz;
+    pc[i] = make_pos4(px, py, pz, 0);
+    if constexpr (P::kFp64) return d2 >= a.thr2;
+    else return d2 >= a.thr2f;
+}
+
 // First half of the first step of an md_step call (Sec. 3.1 (a)): half kick
 // with the stored forces, drift, displacement test.
 template <class P>
@@ -1079,22 +1138,7 @@ __global__ void __launch_bounds__(kBlock) k_kickdrift(Args<P> a, long long nstep
     const int par = vw.par;
     int64_t i = gtid();
     bool far = false;
-    if (!err && i < a.n) {
-        pos4* pc = par ? a.pB : a.pA;
-        vel vx = kick(a, a.vx[i], a.fx[i]);
-        vel vy = kick(a, a.vy[i], a.fy[i]);
-        vel vz = kick(a, a.vz[i], a.fz[i]);
-        double ox = drift(a.ox[i], vx, a.dt);
-        double oy = drift(a.oy[i], vy, a.dt);
-        double oz = drift(a.oz[i], vz, a.dt);
-        real px, py, pz;
-        real d2 = moved(a.pbx[i], ox, px) + moved(a.pby[i], oy, py) + moved(a.pbz[i], oz, pz);
-        a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
-        a.ox[i] = ox; a.oy[i] = oy; a.oz[i] = oz;
-        pc[i] = make_pos4(px, py, pz, 0);
-        if constexpr (P::kFp64) far = d2 >= a.thr2;
-        else far = d2 >= a.thr2f;
-    }
+    if (!err && i < a.n) far = kickdrift_item<P>(a, i, par ? a.pB : a.pA);
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
     if (last_block_done(C)) {
         if (threadIdx.x == 0) {
@@ -1107,70 +1151,51 @@ __global__ void __launch_bounds__(kBlock) k_kickdrift(Args<P> a, long long nstep
     }
 }
 
-// Force + integration kernel (Sec. 3.1 (c)-(e) of one step and (a) of the
-// next).  A full step: forces f_n, v_n = v_{n-1/2} + f_n dt/2,
-// v_{n+1/2} = v_n + f_n dt/2, o += v_{n+1/2} dt into the other pair buffer
-// and the skin/2 test.  The kFinal variant also handles the last step of an
-// md_step call (forces, v_n, PE/W/KE partials, no drift) and mode
-// kModeInit (forces of a freshly loaded state); the plain variant, used for
-// every other step, carries no energy accumulators.  The last block
-// advances the counters and, in a graph, sets the next conditional rebuild.
-template <class P, bool kCells, bool kFinal>
-__global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, int mode, cudaGraphConditionalHandle next,
-                                                 int has_next) {
-    using real = typename P::real;
-    using vel = typename P::vel;
-    using pos4 = typename P::pos4;
-    __shared__ double shs[kBlock / 32];
-    constexpr bool kTable = P::kFp64 && !kCells;  // shift table and pair queue (FP64 list form)
-    __shared__ pos4 s_shift[kTable ? 64 : 1];
-    __shared__ typename Queue<P>::item s_queue[kTable ? Queue<P>::kSlots * kBlock : 1];
-    __shared__ __align__(16) int s_rows[kCells ? 4 : kStageRows * kBlock];
-    Counters* C = a.ctr;
-    if constexpr (kTable) fill_shift_table<P>(a, s_shift);
-    // Requests that do not depend on the counters go out first, so their
-    // latency overlaps the counter read: the first rows of the warp's
-    // neighbour column block (copied to shared memory; rows below the
-    // capacity always exist, unused ones are ignored) and the neighbour
-    // count.  The pair coordinate q_i comes from the current pair buffer
-    // (bit-identical to pb + o rounded, which wrote it); pb and o are read
-    // after the force loop, where they are needed.
-    const int64_t i = gtid();
-    const bool in = i < a.n;
-    int cnt = 0, staged = 0;
-    const int* col = nullptr;
-    int* rows = s_rows + (threadIdx.x >> 5) * (kStageRows * 32);
+// Stages the first rows of the warp's neighbour column block in shared
+// memory (rows below the capacity always exist; unused ones are ignored)
+// and reads atom i's neighbour count.  Every lane of the warp must call it.
+template <class P, bool kCells>
+__device__ __forceinline__ void stage_rows(const Args<P>& a, int64_t i, int* rows, int& cnt, int& staged,
+                                           const int*& col) {
+    cnt = 0;
+    staged = 0;
+    col = nullptr;
     if constexpr (!kCells) {
         if ((i & ~(int64_t)31) < a.n) {  // the warp's column block exists
             staged = min(a.cap, kStageRows);
             const int* blk = a.nbr + (size_t)(i >> 5) * (size_t)a.cap * 32;
             for (int c = threadIdx.x & 31; c < staged * 8; c += 32) cp_async16(rows + 4 * c, blk + 4 * c);
         }
-    }
-    if (in) {
-        if constexpr (!kCells) {
+        if (i < a.n) {
             cnt = a.nn[i];
             col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
         }
     }
-    if constexpr (!kCells) {
+}
+template <bool kCells>
+__device__ __forceinline__ void stage_wait() {
+    if constexpr (!kCells) {  // every lane that issued copies waits for them
         cp_async_wait_all();
         __syncwarp();
     }
-    const View vw = load_view(C);  // also orders the table fill before its use
-    const int err = vw.err;
-    const long long left = vw.left;
-    const int par = vw.par;
-    const bool init = kFinal && (mode == kModeInit);
-    const bool last = kFinal && !init && left == 1;
-    const bool misplaced = !kFinal && left == 1;  // a plain node must never run a call's last step
-    const bool active = init || (err == 0 && left > 0 && !misplaced);
-    const bool energy = init || last;
-    const pos4* pc = par ? a.pB : a.pA;
-    pos4* pn = par ? a.pA : a.pB;
-    bool far = false, close = false;
-    double ke = 0.0, pe = 0.0, vir = 0.0;
-    if (active && in) {
+}
+
+// The per-atom part of a step (Sec. 3.1 (c)-(e) and (a) of the next step):
+// forces of atom i, then either the final-step work (v_n, stored forces,
+// KE/PE/W terms) or the next half kick, the drift into the other pair
+// buffer and the skin/2 test.  Shared by the grid kernel and the
+// per-replica engine.
+template <class P, bool kCells, bool kFinal>
+__device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, bool active, bool init, bool energy,
+                                          int cnt, const int* col, const int* rows, int staged,
+                                          const typename P::pos4* __restrict__ pc, typename P::pos4* pn,
+                                          const typename P::pos4* s_shift, typename Queue<P>::item* s_queue,
+                                          bool& far, bool& close, double& ke, double& pe, double& vir) {
+    using real = typename P::real;
+    using vel = typename P::vel;
+    using pos4 = typename P::pos4;
+    if (!(active && in)) return;
+    {
         const pos4 qi = ld_pos4(pc + i);
         const real qx = qi.x, qy = qi.y, qz = qi.z;
         typename AccOf<P>::type acc;
@@ -1220,6 +1245,58 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
             else far = d2 >= a.thr2f;
         }
     }
+}
+
+// Force + integration kernel (Sec. 3.1 (c)-(e) of one step and (a) of the
+// next).  A full step: forces f_n, v_n = v_{n-1/2} + f_n dt/2,
+// v_{n+1/2} = v_n + f_n dt/2, o += v_{n+1/2} dt into the other pair buffer
+// and the skin/2 test.  The kFinal variant also handles the last step of an
+// md_step call (forces, v_n, PE/W/KE partials, no drift) and mode
+// kModeInit (forces of a freshly loaded state); the plain variant, used for
+// every other step, carries no energy accumulators.  The last block
+// advances the counters and, in a graph, sets the next conditional rebuild.
+template <class P, bool kCells, bool kFinal>
+__global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, int mode, cudaGraphConditionalHandle next,
+                                                 int has_next) {
+    using real = typename P::real;
+    using vel = typename P::vel;
+    using pos4 = typename P::pos4;
+    __shared__ double shs[kBlock / 32];
+    constexpr bool kTable = P::kFp64 && !kCells;  // shift table and pair queue (FP64 list form)
+    __shared__ pos4 s_shift[kTable ? 64 : 1];
+    __shared__ typename Queue<P>::item s_queue[kTable ? Queue<P>::kSlots * kBlock : 1];
+    __shared__ __align__(16) int s_rows[kCells ? 4 : kStageRows * kBlock];
+    Counters* C = a.ctr;
+    if constexpr (kTable) fill_shift_table<P>(a, s_shift);
+    // Requests that do not depend on the counters go out first, so their
+    // latency overlaps the counter read: the first rows of the warp's
+    // neighbour column block (copied to shared memory; rows below the
+    // capacity always exist, unused ones are ignored) and the neighbour
+    // count.  The pair coordinate q_i comes from the current pair buffer
+    // (bit-identical to pb + o rounded, which wrote it); pb and o are read
+    // after the force loop, where they are needed.
+    const int64_t i = gtid();
+    const bool in = i < a.n;
+    int cnt, staged;
+    const int* col;
+    int* rows = s_rows + (threadIdx.x >> 5) * (kStageRows * 32);
+    stage_rows<P, kCells>(a, i, rows, cnt, staged, col);
+    stage_wait<kCells>();
+    const View vw = load_view(C);  // also orders the table fill before its use
+    const int err = vw.err;
+    const long long left = vw.left;
+    const int par = vw.par;
+    const bool init = kFinal && (mode == kModeInit);
+    const bool last = kFinal && !init && left == 1;
+    const bool misplaced = !kFinal && left == 1;  // a plain node must never run a call's last step
+    const bool active = init || (err == 0 && left > 0 && !misplaced);
+    const bool energy = init || last;
+    const pos4* pc = par ? a.pB : a.pA;
+    pos4* pn = par ? a.pA : a.pB;
+    bool far = false, close = false;
+    double ke = 0.0, pe = 0.0, vir = 0.0;
+    step_atom<P, kCells, kFinal>(a, i, in, active, init, energy, cnt, col, rows, staged, pc, pn, s_shift, s_queue,
+                                 far, close, ke, pe, vir);
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
     if (__any_sync(0xffffffffu, close) && (threadIdx.x & 31) == 0) atomicOr(&C->close_flag, 1);
     if constexpr (kFinal) {
@@ -1364,6 +1441,293 @@ __global__ void __launch_bounds__(kBlock) k_selftest(long long n, unsigned long 
 }
 
 // ---------------------------------------------------------------------------
+// ensembles: independent replicas, one thread block each
+// ---------------------------------------------------------------------------
+
+// Block-wide accumulators of the per-replica engine.
+struct EnsShared {
+    long long entries;
+    int far, close, maxv, job;
+    int carry;
+    int warp_tot[32];
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Exclusive scan of the replica's cell counts into cell_start, block-wide,
+// and the largest occupancy (the paper's N_l) into C->max_occ.
+template <class P>
+__device__ __noinline__ void ens_scan(const Args<P>& a, EnsShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) sh.carry = 0;
+    int mx = 0;
+    __syncthreads();
+    for (int base = 0; base < a.ncells; base += blockDim.x) {
+        const int c = base + threadIdx.x;
+        const int v = c < a.ncells ? a.count[c] : 0;
+        mx = max(mx, v);
+        int x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sh.warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int t = lane < nw ? sh.warp_tot[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            sh.warp_tot[lane] = t;  // inclusive over warps
+        }
+        __syncthreads();
+        const int excl = x - v + (warp > 0 ? sh.warp_tot[warp - 1] : 0) + sh.carry;
+        if (c < a.ncells) a.cell_start[c] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) sh.carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.cell_start[a.ncells] = (int)a.n;
+        sh.maxv = 0;
+        sh.entries = 0;
+    }
+    __syncthreads();
+    atomicMax(&sh.maxv, mx);
+    __syncthreads();
+    if (threadIdx.x == 0) a.ctr->max_occ = sh.maxv;
+}
+
+// The rebuild branch of one replica (the kernels k_bin .. k_rebuild_done,
+// block-wide with barriers between the phases).
+template <class P>
+__device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh) {
+    Counters* C = a.ctr;
+    const int64_t n = a.n, t0 = threadIdx.x, dt = blockDim.x;
+    for (int64_t i = t0; i < n; i += dt) bin_item<P>(a, i);
+    __syncthreads();
+    ens_scan<P>(a, sh);
+    for (int64_t t = t0; t < n; t += dt) scatter_item<P>(a, t);
+    for (int64_t c = t0; c < a.ncells; c += dt) a.count[c] = 0;
+    __syncthreads();
+    for (int64_t c = t0; c < a.ncells; c += dt) cellsort_item<P>(a, c);
+    __syncthreads();
+    for (int64_t s = t0; s < n; s += dt) gather_item<P>(a, s);
+    __syncthreads();
+    if (C->reorder_now) {
+        for (int64_t s = t0; s < n; s += dt) commit_item<P>(a, s);
+        __syncthreads();
+    }
+    int mx = 0;
+    long long sum = 0;
+    for (int64_t s = t0; s < n; s += dt) {
+        const int m = build_item<P>(a, s);
+        mx = max(mx, m);
+        sum += m;
+    }
+    atomicMax(&sh.maxv, mx);
+    atomicAdd((unsigned long long*)&sh.entries, (unsigned long long)sum);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        C->max_nn = sh.maxv;
+        C->list_entries = sh.entries;
+        C->rebuilds += 1;
+        if (C->reorder_now) {
+            C->reorders += 1;
+            C->since_reorder = 0;
+            C->reorder_now = 0;
+        }
+        C->rebuild_flag = 0;
+    }
+    __syncthreads();
+}
+
+// One step of one replica (k_step, block-wide): warps take 32 atoms at a
+// time, stage their list rows, compute forces and integrate; then the
+// counters advance as in k_step's last block.  kFinal: the init or last step.
+template <class P, bool kFinal>
+__device__ __noinline__ void ens_step(const Args<P>& a, EnsShared& sh, int* rows, bool init) {
+    Counters* C = a.ctr;
+    const int err = C->error;
+    const long long left = C->steps_left;
+    const int par = C->parity;
+    const bool last = kFinal && !init && left == 1;
+    const bool active = init || (err == 0 && left > 0);
+    const bool energy = init || last;
+    const typename P::pos4* pc = par ? a.pB : a.pA;
+    typename P::pos4* pn = par ? a.pA : a.pB;
+    if (threadIdx.x == 0) {
+        sh.far = 0;
+        sh.close = 0;
+    }
+    __syncthreads();
+    bool far = false, close = false;
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int64_t nchunks = (a.n + 31) / 32;
+    for (int64_t ch = threadIdx.x >> 5; ch < nchunks; ch += nw) {
+        const int64_t i = ch * 32 + lane;
+        int cnt, staged;
+        const int* col;
+        stage_rows<P, false>(a, i, rows, cnt, staged, col);
+        stage_wait<false>();
+        bool f = false, cl = false;
+        double k = 0.0, u = 0.0, w = 0.0;
+        step_atom<P, false, kFinal>(a, i, i < a.n, active, init, energy, cnt, col, rows, staged, pc, pn, nullptr,
+                                    nullptr, f, cl, k, u, w);
+        far |= f;
+        close |= cl;
+        if (kFinal && energy) {  // fixed-shape sum over the chunk's 32 atoms
+            for (int o = 16; o > 0; o >>= 1) {
+                k += __shfl_xor_sync(0xffffffffu, k, o);
+                u += __shfl_xor_sync(0xffffffffu, u, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+            if (lane == 0) {
+                a.part[3 * ch + 0] = k;
+                a.part[3 * ch + 1] = u;
+                a.part[3 * ch + 2] = w;
+            }
+        }
+        __syncwarp();  // the next chunk's copies overwrite rows
+    }
+    if (__any_sync(0xffffffffu, far) && lane == 0) atomicOr(&sh.far, 1);
+    if (__any_sync(0xffffffffu, close) && lane == 0) atomicOr(&sh.close, 1);
+    __syncthreads();
+    if (kFinal && energy) {
+        // chunk sums -> sums of 32 consecutive chunks (fixed shape, in any
+        // warp) -> their sum in order: the same numbers whatever the launch
+        const int64_t ngroups = (nchunks + 31) / 32;
+        double* gsum = a.part + 3 * nchunks;
+        for (int64_t g = threadIdx.x >> 5; g < ngroups; g += nw) {
+            const int64_t c = g * 32 + lane;
+            double k = c < nchunks ? a.part[3 * c + 0] : 0.0;
+            double u = c < nchunks ? a.part[3 * c + 1] : 0.0;
+            double w = c < nchunks ? a.part[3 * c + 2] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                k += __shfl_xor_sync(0xffffffffu, k, o);
+                u += __shfl_xor_sync(0xffffffffu, u, o);
+                w += __shfl_xor_sync(0xffffffffu, w, o);
+            }
+            if (lane == 0) {
+                gsum[3 * g + 0] = k;
+                gsum[3 * g + 1] = u;
+                gsum[3 * g + 2] = w;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (sh.far) C->far_flag = 1u;
+        if (active && !init) {
+            C->steps_left = left - 1;
+            C->step += 1;
+            C->since_reorder += 1;
+            if (!last) {
+                C->parity = par ^ 1;
+                decide_rebuild(C, a.cell_list_only, a.reorder_interval);
+            } else {
+                C->far_flag = 0u;
+                C->rebuild_flag = 0;
+            }
+        } else if (!init) {
+            C->far_flag = 0u;
+        }
+        if (sh.close) C->error |= kErrClose;
+        if (kFinal && energy && active) {
+            const int64_t nchunks_ = (a.n + 31) / 32, ngroups = (nchunks_ + 31) / 32;
+            const double* gsum = a.part + 3 * nchunks_;
+            double k = 0.0, u = 0.0, w = 0.0;
+            for (int64_t g = 0; g < ngroups; g++) {
+                k += gsum[3 * g + 0];
+                u += gsum[3 * g + 1];
+                w += gsum[3 * g + 2];
+            }
+            C->ke = k;
+            C->pe = u;
+            C->virial = w;
+        }
+    }
+    __syncthreads();
+}
+
+// The per-replica engine: each block takes jobs from a queue (jobs are in
+// decreasing order of work) and runs one replica at a time from load to its
+// last step -- md_set_state and md_step for that replica, with block
+// barriers where the single-simulation path has kernel boundaries.
+// Dynamic shared memory: kStageRows x 32 ints per warp.
+template <class P>
+__global__ void __launch_bounds__(1024, 1) k_ensemble(const Args<P>* __restrict__ reps, EnsJob* jobs, int njobs,
+                                                       int* next) {
+    extern __shared__ __align__(16) int ens_rows[];
+    __shared__ EnsShared sh;
+    __shared__ __align__(16) Args<P> a;
+    int* rows = ens_rows + (threadIdx.x >> 5) * (kStageRows * 32);
+    for (;;) {
+        if (threadIdx.x == 0) sh.job = atomicAdd(next, 1);
+        __syncthreads();
+        const int j = sh.job;
+        if (j >= njobs) return;
+        {  // the replica's arguments, copied by the whole block in 16-byte words
+            static_assert(sizeof(Args<P>) % 16 == 0, "Args must be a whole number of 16-byte words");
+            const int4* src = reinterpret_cast<const int4*>(reps + jobs[j].rep);
+            int4* dst = reinterpret_cast<int4*>(&a);
+            for (int k = threadIdx.x; k < (int)(sizeof(Args<P>) / 16); k += blockDim.x) dst[k] = src[k];
+        }
+        if (threadIdx.x == 0) jobs[j].t_start = globaltimer_ns();
+        __syncthreads();
+        Counters* C = a.ctr;
+        if (jobs[j].init) {
+            {  // counters of a freshly loaded state: a rebuild with reorder is pending
+                static_assert(sizeof(Counters) % 8 == 0, "Counters must be a whole number of 8-byte words");
+                long long* w = reinterpret_cast<long long*>(C);
+                for (int k = threadIdx.x; k < (int)(sizeof(Counters) / 8); k += blockDim.x) w[k] = 0;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    C->rebuild_flag = 1;
+                    C->reorder_now = 1;
+                }
+            }
+            __syncthreads();
+            for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) set_state_item<P>(a, i);
+            __syncthreads();
+            if (C->error == 0) ens_rebuild<P>(a, sh);
+            if (C->error == 0) ens_step<P, true>(a, sh, rows, true);
+        }
+        const long long nsteps = jobs[j].nsteps;
+        if (nsteps > 0 && C->error == 0) {
+            if (threadIdx.x == 0) sh.far = 0;
+            __syncthreads();
+            bool far = false;
+            const int par = C->parity;
+            for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) far |= kickdrift_item<P>(a, i, par ? a.pB : a.pA);
+            if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&sh.far, 1);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (sh.far) C->far_flag = 1u;
+                C->steps_left = nsteps;
+                decide_rebuild(C, a.cell_list_only, a.reorder_interval);
+            }
+            __syncthreads();
+            for (long long st = 0; st < nsteps; st++) {
+                if (C->rebuild_flag) ens_rebuild<P>(a, sh);
+                if (C->error) break;
+                if (st + 1 < nsteps) ens_step<P, false>(a, sh, rows, false);
+                else ens_step<P, true>(a, sh, rows, false);
+                if (C->error) break;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) jobs[j].t_end = globaltimer_ns();
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // kernel table used by the host runtime (graph nodes and eager launches)
 // ---------------------------------------------------------------------------
 
@@ -1394,6 +1758,8 @@ KernelTable<P> make_kernel_table() {
     t.reset_counters = (void*)k_reset_counters<P>;
     t.clear_overflow = (void*)k_clear_overflow<P>;
     t.selftest = (void*)k_selftest<P>;
+    if constexpr (!P::kFp64) t.ensemble = (void*)k_ensemble<P>;
+    else t.ensemble = nullptr;
     return t;
 }
 

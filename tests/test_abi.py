@@ -47,7 +47,7 @@ def test_struct_layouts_match_header(tmp_path):
     # compile a probe against include/md.h and compare sizes and offsets
     import ctypes as C
     import subprocess
-    structs = [md.md_params, md.md_plan_t, md.md_measure_t, md.md_kernel_stats_t]
+    structs = [md.md_params, md.md_plan_t, md.md_measure_t, md.md_kernel_stats_t, md.md_replica_desc]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "md.h"', 'int main(void) {']
     for s in structs:
         lines.append('printf("%%zu\\n", sizeof(%s));' % s.__name__)
@@ -120,3 +120,17 @@ def test_default_params(libmd):
     p = md.md_default_params()
     assert p.precision == md.MD_PREC_MIXED and p.reorder_interval == 100 and p.use_graphs == 1
     assert np.isnan(p.ushift) and p.device == -1
+
+
+def test_ensemble_replica_bytes_needs_no_gpu(libmd):
+    small = md.replica_desc([8.0] * 3, 410)
+    big = md.replica_desc([32.0] * 3, 26214)
+    b0, b1 = md.md_ensemble_replica_bytes(small), md.md_ensemble_replica_bytes(big)
+    assert 0 < b0 < b1
+    # roughly the per-atom state plus the list: a few hundred bytes per atom
+    assert 150 * 26214 < b1 < 2000 * 26214
+    bad = md.replica_desc([8.0] * 3, 410)
+    bad.reserved[0] = 1
+    assert md.md_ensemble_replica_bytes(bad) == 0
+    assert md.md_ensemble_replica_bytes(md.replica_desc([8.0] * 3, 410, skin=0.0)) == 0  # list form only
+    assert md.md_ensemble_replica_bytes(md.replica_desc([4.0] * 3, 50)) == 0  # fewer than 3 cells
