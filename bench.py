@@ -51,6 +51,13 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble line")
+    ap.add_argument("--ens-replicas", type=int, default=inputs.ENSEMBLE["replicas"])
+    ap.add_argument("--ens-steps", type=int, default=inputs.ENSEMBLE["steps"])
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace lines")
+    ap.add_argument("--serve-requests", type=int, default=48)
+    ap.add_argument("--serve-low-rate", type=float, default=10.0,
+                    help="arrival rate of the second, below-saturation trace")
     ap.add_argument("--eager", action="store_true", help="stream launches instead of graphs")
     ap.add_argument("--profile-steps", type=int, default=2,
                     help="benchmark steps run with per-kernel CUDA events for the roofline")
@@ -213,6 +220,74 @@ def cpu_baseline(pos, vel, L, cfg, seconds=15.0):
                       "single-threaded C oracle, %.1f s" % (steps, n, t)}
 
 
+def ensemble_bench(md, torch, stream, device, replicas, steps, probe):
+    """The batched ensemble: replicas of uneven size and state, loaded into
+    one arena, autotuned, then advanced `steps` steps each by one launch.
+    Latency = each replica's completion time after the launch began."""
+    specs = inputs.ensemble_specs(replicas)
+    skin, reorder = inputs.ENSEMBLE["skin"], inputs.ENSEMBLE["reorder_interval"]
+    states = [inputs.wca_state(n, rho, T, seed) for (n, rho, T, seed) in specs]
+    need = sum(md.md_ensemble_replica_bytes(md.replica_desc(L, p.shape[0], RC, skin, DT, reorder))
+               for (p, v, L) in states)
+    e = md.Ensemble(int(need * 1.02) + (256 << 20), max_replicas=replicas, device=device,
+                    stream=stream.cuda_stream)
+    try:
+        ids = [e.add(p, v, L, RC, skin, DT, reorder_interval=reorder) for (p, v, L) in states]
+        atoms = sum(p.shape[0] for (p, v, L) in states)
+        e.run(ids, [0] * len(ids))  # load: wrap, bin, list, forces
+        e.sync()
+        block, _ = e.autotune(ids, probe_steps=probe)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        e.run(ids, [steps] * len(ids))
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        t0, t1 = e.times(ids)
+        bad = [i for i in ids if e.status(i) != md.MD_OK]
+        if bad:
+            raise RuntimeError("ensemble replicas failed: %s" % bad[:8])
+        m = e.measure(ids[0])
+        if m["step"] != steps + 4 * probe:
+            raise RuntimeError("ensemble replica advanced %d steps" % m["step"])
+        return {"workload": "wca_ensemble_%d" % replicas, "replicas": replicas, "atoms": int(atoms),
+                "n_range": [inputs.ENSEMBLE["n_min"], inputs.ENSEMBLE["n_max"]], "steps": steps,
+                "value": atoms * steps / (ms / 1e3), "unit": UNIT, "ms": ms, "launches": 1,
+                "latency_p50_ms": float(np.percentile(t1, 50)), "latency_p99_ms": float(np.percentile(t1, 99)),
+                "latency_max_ms": float(np.max(t1)),
+                "latency": "completion of each replica after the launch began; all replicas submitted together",
+                "block": int(block), "autotune_probe_steps": probe}
+    finally:
+        e.close()
+
+
+def serving_bench(md, stream, device, count, rate, budget_bytes, slice_steps):
+    """Replays a Poisson trace of `count` requests through the
+    continuous-batching loop (paper_0911_5631_gb300.serve)."""
+    from paper_0911_5631_gb300.serve import Request, Server
+    sk = inputs.SERVING["skin"]
+    reqs = []
+    for k, (t, n, rho, T, seed, ns) in enumerate(inputs.serving_trace(count, rate=rate)):
+        pos, vel, L = inputs.wca_state(n, rho, T, seed)
+        reqs.append(Request(key=k, pos=pos, vel=vel, box=L, nsteps=ns, arrival=t, skin=sk, dt=DT))
+    srv = Server(budget_bytes, slice_steps=slice_steps, device=device, keep_results=False)
+    try:
+        st = srv.serve(reqs)
+    finally:
+        srv.close()
+    if st["failed"]:
+        raise RuntimeError("%d serving requests failed" % st["failed"])
+    st.update({"workload": "wca_serving_poisson", "rate_per_s": rate, "requests_offered": count,
+               "n_range": [inputs.SERVING["n_min"], inputs.SERVING["n_max"]],
+               "steps_range": list(inputs.SERVING["steps"]), "slice_steps": slice_steps,
+               "budget_gb": budget_bytes / 1e9,
+               "offered_atom_steps_per_s": rate * float(np.mean([r.atoms * r.nsteps for r in reqs])),
+               "latency": "completion - arrival (s), trace replayed in real time"})
+    return st
+
+
 def run_ours(args):
     import torch
     import paper_0911_5631_gb300 as md
@@ -352,6 +427,13 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         cpu = cpu_baseline(eq_pos, eq_vel, L, cfg)
 
+    ens = None
+    if rank == 0 and not args.no_ensemble:
+        ens = ensemble_bench(md, torch, stream, local, args.ens_replicas, args.ens_steps, 10)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = [serving_bench(md, stream, local, args.serve_requests, rate, 40 << 30, 200)
+                   for rate in (inputs.SERVING["rate"], args.serve_low_rate)]
     if rank == 0:
         ws_bytes = n * (12 + 24 + 12 + 32 + 4) + list_entries * 4 * 1.3
         line = {
@@ -373,6 +455,8 @@ def run_ours(args):
             "fp64_form": fp64,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "ensemble": ens,
+            "serving": serving,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

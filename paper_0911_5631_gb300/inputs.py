@@ -125,3 +125,45 @@ WORKLOADS = {
     "wca_fcc128_n8m_rho0.6_T0.7": dict(n=8388608, rho=0.6, T=0.7, seed=3, skin=0.4, steps=100000),
     "wca_fcc128_n8m_rho1.0_T2.0": dict(n=8388608, rho=1.0, T=2.0, seed=3, skin=0.4, steps=100000),
 }
+
+
+# Batched ensemble: independent WCA replicas of uneven size and state.
+ENSEMBLE = dict(replicas=512, n_min=256, n_max=32768, rho=(0.6, 1.0), T=(0.5, 2.0), seed=4, skin=0.4,
+                steps=2000, reorder_interval=100)
+
+
+def ensemble_specs(replicas: int = ENSEMBLE["replicas"], seed: int = ENSEMBLE["seed"],
+                   n_min: int = ENSEMBLE["n_min"], n_max: int = ENSEMBLE["n_max"]):
+    """Per-replica (n, rho, T, seed): n log-uniform in [n_min, n_max], rho and
+    T uniform in the ENSEMBLE ranges, all from one seeded SplitMix64 stream."""
+    u = uniform(seed, 3 * replicas).reshape(replicas, 3)
+    lo, hi = np.log(n_min), np.log(n_max)
+    out = []
+    for k in range(replicas):
+        n = int(np.floor(np.exp(lo + (hi - lo) * u[k, 0])))
+        n = min(max(n, n_min), n_max)
+        rho = ENSEMBLE["rho"][0] + (ENSEMBLE["rho"][1] - ENSEMBLE["rho"][0]) * u[k, 1]
+        T = ENSEMBLE["T"][0] + (ENSEMBLE["T"][1] - ENSEMBLE["T"][0]) * u[k, 2]
+        out.append((n, float(rho), float(T), seed * 100003 + k))
+    return out
+
+
+# Serving trace: Poisson arrivals of independent WCA requests.
+SERVING = dict(rate=200.0, n_min=500, n_max=200000, steps=(1000, 20000), rho=0.8, T=1.0, seed=5, skin=0.4)
+
+
+def serving_trace(count: int, rate: float = SERVING["rate"], seed: int = SERVING["seed"],
+                  n_min: int = SERVING["n_min"], n_max: int = SERVING["n_max"], steps=SERVING["steps"]):
+    """count requests (arrival_s, n, rho, T, seed, nsteps): exponential
+    inter-arrival times of mean 1/rate, n log-uniform in [n_min, n_max],
+    nsteps uniform in [steps[0], steps[1]], the state (rho, T) of SERVING."""
+    u = uniform(seed, 3 * count).reshape(count, 3)
+    t = np.cumsum(-np.log(u[:, 0]) / rate)
+    lo, hi = np.log(n_min), np.log(n_max)
+    out = []
+    for k in range(count):
+        n = min(max(int(np.floor(np.exp(lo + (hi - lo) * u[k, 1]))), n_min), n_max)
+        ns = int(steps[0] + np.floor((steps[1] - steps[0] + 1) * (1.0 - u[k, 2])))
+        ns = min(max(ns, steps[0]), steps[1])
+        out.append((float(t[k]), n, SERVING["rho"], SERVING["T"], seed * 1000003 + k, ns))
+    return out
