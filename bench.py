@@ -236,7 +236,7 @@ def ensemble_bench(md, torch, stream, device, replicas, steps, probe):
         atoms = sum(p.shape[0] for (p, v, L) in states)
         e.run(ids, [0] * len(ids))  # load: wrap, bin, list, forces
         e.sync()
-        block, _ = e.autotune(ids, probe_steps=probe)
+        block, cluster = e.autotune(ids, probe_steps=probe)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -250,7 +250,7 @@ def ensemble_bench(md, torch, stream, device, replicas, steps, probe):
         if bad:
             raise RuntimeError("ensemble replicas failed: %s" % bad[:8])
         m = e.measure(ids[0])
-        if m["step"] != steps + 4 * probe:
+        if m["step"] != steps + 5 * probe:
             raise RuntimeError("ensemble replica advanced %d steps" % m["step"])
         return {"workload": "wca_ensemble_%d" % replicas, "replicas": replicas, "atoms": int(atoms),
                 "n_range": [inputs.ENSEMBLE["n_min"], inputs.ENSEMBLE["n_max"]], "steps": steps,
@@ -258,7 +258,7 @@ def ensemble_bench(md, torch, stream, device, replicas, steps, probe):
                 "latency_p50_ms": float(np.percentile(t1, 50)), "latency_p99_ms": float(np.percentile(t1, 99)),
                 "latency_max_ms": float(np.max(t1)),
                 "latency": "completion of each replica after the launch began; all replicas submitted together",
-                "block": int(block), "autotune_probe_steps": probe}
+                "block": int(block), "cluster": int(cluster), "autotune_probe_steps": probe}
     finally:
         e.close()
 

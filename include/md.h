@@ -331,16 +331,19 @@ int md_ensemble_get_state(md_ensemble* e, int32_t id, double* pos, double* vel);
 int md_ensemble_times(md_ensemble* e, int32_t count, const int32_t* ids, double* start_ms, double* end_ms);
 
 /* Launch shape for md_ensemble_run: threads per block (a multiple of 32,
- * 64 .. 1024) and blocks (0: as many as fit on the device at once).
- * block 0 restores the default (256). */
-int md_ensemble_set_shape(md_ensemble* e, int32_t block, int32_t grid);
+ * 64 .. 1024; 0: 256), blocks (0: as many as fit on the device at once),
+ * and teams: a replica of at least team_atoms atoms (0: 8192) is run by a
+ * thread-block cluster of `cluster` blocks (1 .. 8; 0: 8) that split its
+ * atoms and meet at hardware cluster barriers, so one big replica is not
+ * limited to one SM; cluster 1 gives every replica one block. */
+int md_ensemble_set_shape(md_ensemble* e, int32_t block, int32_t grid, int32_t cluster, int64_t team_atoms);
 
-/* Autotuner: runs ids for probe_steps steps under each candidate launch
- * shape (these are real steps: the replicas advance by
- * probe_steps x number of candidates), keeps the fastest shape and returns
- * it in *block, *grid (either may be NULL). */
+/* Autotuner: runs ids for probe_steps steps under each candidate
+ * (threads per block, cluster) pair (these are real steps: the replicas
+ * advance by probe_steps x number of candidates, 5), keeps the fastest
+ * and returns it in *block, *cluster (either may be NULL). */
 int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int64_t probe_steps,
-                         int32_t* block, int32_t* grid);
+                         int32_t* block, int32_t* cluster);
 
 /* Arena bytes a replica of this description needs (0 on a bad one), and
  * the largest free arena block right now. */

@@ -160,7 +160,7 @@ SIGNATURES = [
     ("md_ensemble_measure", C.c_int, [_H, C.c_int32, C.POINTER(md_measure_t)]),
     ("md_ensemble_get_state", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_void_p]),
     ("md_ensemble_times", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
-    ("md_ensemble_set_shape", C.c_int, [_H, C.c_int32, C.c_int32]),
+    ("md_ensemble_set_shape", C.c_int, [_H, C.c_int32, C.c_int32, C.c_int32, C.c_int64]),
     ("md_ensemble_autotune", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_int64, C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int32)]),
     ("md_ensemble_replica_bytes", C.c_int64, [C.POINTER(md_replica_desc)]),
@@ -519,8 +519,9 @@ class Ensemble:
                    self.e)
         return t0, t1
 
-    def set_shape(self, block=0, grid=0):
-        _ens_check(lib().md_ensemble_set_shape(self.e, int(block), int(grid)), self.e)
+    def set_shape(self, block=0, grid=0, cluster=0, team_atoms=0):
+        _ens_check(lib().md_ensemble_set_shape(self.e, int(block), int(grid), int(cluster), int(team_atoms)),
+                   self.e)
 
     def autotune(self, ids, probe_steps=20):
         ids = np.ascontiguousarray(ids, dtype=np.int32)

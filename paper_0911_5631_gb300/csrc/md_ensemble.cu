@@ -175,6 +175,8 @@ struct md_ensemble {
     std::vector<Replica> reps;
     KernelTable<Mixed> kt{};
     int block = 256, grid = 0;
+    int cluster = 8;            // blocks per team for big replicas (1: no teams)
+    int64_t team_atoms = 8192;  // replicas with at least this many atoms get a team
     std::string err;
 };
 
@@ -249,31 +251,57 @@ int read_counters(md_ensemble* e, const Replica& rp, Counters* c) {
     return MD_OK;
 }
 
-int launch_run(md_ensemble* e, const std::vector<EnsJob>& jobs, int block, int grid) {
+int launch_run(md_ensemble* e, const std::vector<EnsJob>& jobs, int nteam, int block, int grid, int cluster) {
     int r = ensure_jobs(e, (int)jobs.size());
     if (r) return r;
     // from pageable memory: the call has read `jobs` when it returns
     ENS_CUDA(cudaMemcpyAsync(e->d_jobs, jobs.data(), sizeof(EnsJob) * jobs.size(), cudaMemcpyHostToDevice, e->stream));
-    ENS_CUDA(cudaMemsetAsync(e->d_next, 0, sizeof(int), e->stream));
+    ENS_CUDA(cudaMemsetAsync(e->d_next, 0, 2 * sizeof(int), e->stream));
     int nj = (int)jobs.size();
+    if (nteam == 0) cluster = 1;
     size_t smem = (size_t)(block / 32) * kStageRows * 32 * sizeof(int);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = e->stream;
+    if (cluster > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
     int g = grid;
     if (g <= 0) {
-        int per_sm = 0, sms = 0;
-        ENS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)e->kt.ensemble, block, smem));
-        ENS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
-        g = std::max(1, per_sm) * sms;
+        if (cluster > 1) {
+            int nclusters = 0;
+            cfg.gridDim = dim3(cluster);
+            ENS_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, (const void*)e->kt.ensemble, &cfg));
+            g = std::max(1, nclusters) * cluster;
+        } else {
+            int per_sm = 0, sms = 0;
+            ENS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)e->kt.ensemble, block, smem));
+            ENS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, e->device));
+            g = std::max(1, per_sm) * sms;
+        }
     }
-    g = std::min(g, nj);
-    void* args[] = {(void*)&e->d_args, (void*)&e->d_jobs, (void*)&nj, (void*)&e->d_next};
-    ENS_CUDA(cudaLaunchKernel(e->kt.ensemble, dim3(g), dim3(block), args, smem, e->stream));
+    // no more blocks than work for them (teams count as `cluster` blocks)
+    const int useful = nteam * cluster + (nj - nteam);
+    g = std::min(g, std::max(useful, cluster));
+    if (cluster > 1) g = (g + cluster - 1) / cluster * cluster;
+    cfg.gridDim = dim3(g);
+    void* args[] = {(void*)&e->d_args, (void*)&e->d_jobs, (void*)&nj, (void*)&nteam, (void*)&e->d_next};
+    ENS_CUDA(cudaLaunchKernelExC(&cfg, e->kt.ensemble, args));
     e->last_njobs = nj;
     e->jobs_valid = false;
     e->runs++;
     return MD_OK;
 }
 
-int make_jobs(md_ensemble* e, int32_t count, const int32_t* ids, const int64_t* nsteps, std::vector<EnsJob>* jobs) {
+int make_jobs(md_ensemble* e, int32_t count, const int32_t* ids, const int64_t* nsteps, std::vector<EnsJob>* jobs,
+              int cluster, int* nteam) {
     if (count < 0 || (count > 0 && (!ids || !nsteps))) {
         e->err = "bad id list";
         return MD_EINVAL;
@@ -298,18 +326,24 @@ int make_jobs(md_ensemble* e, int32_t count, const int32_t* ids, const int64_t* 
         j.nsteps = nsteps[k];
         jobs->push_back(j);
     }
-    // largest work first: blocks that take small jobs later fill the gaps
+    // replicas big enough for a team first, then the rest; largest work
+    // first within each list, so that blocks taking small jobs later fill
+    // the gaps
+    auto team = [&](const EnsJob& x) { return cluster > 1 && e->reps[x.rep].a.n >= e->team_atoms; };
     std::stable_sort(jobs->begin(), jobs->end(), [&](const EnsJob& x, const EnsJob& y) {
+        if (team(x) != team(y)) return team(x);
         double wx = (double)e->reps[x.rep].a.n * (double)(x.nsteps + x.init);
         double wy = (double)e->reps[y.rep].a.n * (double)(y.nsteps + y.init);
         return wx > wy;
     });
+    *nteam = 0;
+    for (auto& j : *jobs) *nteam += team(j) ? 1 : 0;
     return MD_OK;
 }
 
-int run_jobs(md_ensemble* e, std::vector<EnsJob>& jobs, int block, int grid) {
+int run_jobs(md_ensemble* e, std::vector<EnsJob>& jobs, int nteam, int block, int grid, int cluster) {
     if (jobs.empty()) return MD_OK;
-    int r = launch_run(e, jobs, block, grid);
+    int r = launch_run(e, jobs, nteam, block, grid, cluster);
     if (r) return r;
     for (size_t k = 0; k < jobs.size(); k++) {
         Replica& rp = e->reps[jobs[k].rep];
@@ -373,7 +407,7 @@ int md_ensemble_create(int64_t arena_bytes, int32_t max_replicas, int32_t device
     e->arena_bytes = arena_bytes;
     e->alloc.reset(arena_bytes);
     if (cudaMalloc(&e->d_args, sizeof(A) * (size_t)max_replicas) != cudaSuccess ||
-        cudaMalloc(&e->d_next, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&e->d_next, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         e->err = "cannot allocate the replica table";
         return fail(MD_ENOMEM);
@@ -485,9 +519,10 @@ int md_ensemble_run(md_ensemble* e, int32_t count, const int32_t* ids, const int
     if (!e) return MD_EINVAL;
     EnsDev dg(e->device);
     std::vector<EnsJob> jobs;
-    int r = make_jobs(e, count, ids, nsteps, &jobs);
+    int nteam = 0;
+    int r = make_jobs(e, count, ids, nsteps, &jobs, e->cluster, &nteam);
     if (r) return r;
-    return run_jobs(e, jobs, e->block, e->grid);
+    return run_jobs(e, jobs, nteam, e->block, e->grid, e->cluster);
 }
 
 int md_ensemble_sync(md_ensemble* e) {
@@ -602,53 +637,59 @@ int md_ensemble_times(md_ensemble* e, int32_t count, const int32_t* ids, double*
     return MD_OK;
 }
 
-int md_ensemble_set_shape(md_ensemble* e, int32_t block, int32_t grid) {
+int md_ensemble_set_shape(md_ensemble* e, int32_t block, int32_t grid, int32_t cluster, int64_t team_atoms) {
     if (!e) return MD_EINVAL;
     if (block == 0) block = 256;
-    if (block < 64 || block > 1024 || block % 32 != 0 || grid < 0) {
-        e->err = "block must be a multiple of 32 in 64..1024 and grid >= 0";
+    if (cluster == 0) cluster = 8;
+    if (team_atoms == 0) team_atoms = 8192;
+    if (block < 64 || block > 1024 || block % 32 != 0 || grid < 0 || cluster < 1 || cluster > 8 ||
+        team_atoms < 0) {
+        e->err = "block must be a multiple of 32 in 64..1024, grid >= 0, cluster in 1..8, team_atoms >= 0";
         return MD_EINVAL;
     }
     e->block = block;
     e->grid = grid;
+    e->cluster = cluster;
+    e->team_atoms = team_atoms;
     return MD_OK;
 }
 
 int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int64_t probe_steps, int32_t* block,
-                         int32_t* grid) {
+                         int32_t* cluster) {
     if (!e) return MD_EINVAL;
     if (probe_steps <= 0) {
         e->err = "probe_steps must be positive";
         return MD_EINVAL;
     }
     EnsDev dg(e->device);
+    int nteam = 0;
     {  // load pending replicas first, so that every candidate times the same work
         std::vector<int64_t> zero(count, 0);
         std::vector<EnsJob> jobs;
-        int r0 = make_jobs(e, count, ids, zero.data(), &jobs);
+        int r0 = make_jobs(e, count, ids, zero.data(), &jobs, e->cluster, &nteam);
         if (r0) return r0;
         bool pending = false;
         for (auto& j : jobs) pending |= j.init != 0;
         if (pending) {
-            r0 = run_jobs(e, jobs, e->block, e->grid);
+            r0 = run_jobs(e, jobs, nteam, e->block, e->grid, e->cluster);
             if (r0) return r0;
         }
     }
     std::vector<int64_t> steps(count, probe_steps);
-    // candidate shapes: threads per block at full occupancy of the SM
-    const int cands[] = {128, 256, 512, 1024};
+    // candidate shapes: (threads per block, blocks per team of a big replica)
+    const int cands[][2] = {{256, 1}, {1024, 1}, {1024, 4}, {1024, 8}, {512, 8}};
     float best = -1.f;
-    int best_b = e->block;
+    int best_b = e->block, best_c = e->cluster;
     cudaEvent_t t0, t1;
     ENS_CUDA(cudaEventCreate(&t0));
     ENS_CUDA(cudaEventCreate(&t1));
     int r = MD_OK;
-    for (int b : cands) {
+    for (auto& c : cands) {
         std::vector<EnsJob> jobs;
-        r = make_jobs(e, count, ids, steps.data(), &jobs);
+        r = make_jobs(e, count, ids, steps.data(), &jobs, c[1], &nteam);
         if (r) break;
         if (cudaEventRecord(t0, e->stream) != cudaSuccess) { r = MD_ECUDA; break; }
-        r = run_jobs(e, jobs, b, 0);
+        r = run_jobs(e, jobs, nteam, c[0], 0, c[1]);
         if (r) break;
         if (cudaEventRecord(t1, e->stream) != cudaSuccess || cudaEventSynchronize(t1) != cudaSuccess) {
             r = MD_ECUDA;
@@ -658,7 +699,8 @@ int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int6
         cudaEventElapsedTime(&ms, t0, t1);
         if (best < 0.f || ms < best) {
             best = ms;
-            best_b = b;
+            best_b = c[0];
+            best_c = c[1];
         }
     }
     cudaEventDestroy(t0);
@@ -669,8 +711,9 @@ int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int6
     }
     e->block = best_b;
     e->grid = 0;
+    e->cluster = best_c;
     if (block) *block = best_b;
-    if (grid) *grid = 0;
+    if (cluster) *cluster = best_c;
     return MD_OK;
 }
 

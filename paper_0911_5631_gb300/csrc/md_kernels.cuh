@@ -1441,13 +1441,51 @@ __global__ void __launch_bounds__(kBlock) k_selftest(long long n, unsigned long 
 }
 
 // ---------------------------------------------------------------------------
-// ensembles: independent replicas, one thread block each
+// ensembles: independent replicas, one thread block (or one cluster) each
 // ---------------------------------------------------------------------------
 
-// Block-wide accumulators of the per-replica engine.
+// The blocks that work on one replica: one thread block, or every block of
+// a thread-block cluster (rank 0 leads).  Barriers between phases are block
+// barriers or cluster barriers (hardware barrier.cluster: no polling).
+struct Team {
+    int rank, size;
+    __device__ __forceinline__ bool lead_block() const { return rank == 0; }
+    __device__ __forceinline__ bool leader() const { return rank == 0 && threadIdx.x == 0; }
+    __device__ __forceinline__ int64_t first(int64_t per_block = 0) const {
+        return (int64_t)rank * blockDim.x + threadIdx.x;
+    }
+    __device__ __forceinline__ int64_t stride() const { return (int64_t)size * blockDim.x; }
+    __device__ __forceinline__ void sync() const {
+        if (size > 1) {
+            asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        } else {
+            __syncthreads();
+        }
+    }
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// Reads an int from the shared memory of block `rank` of this cluster.
+__device__ __forceinline__ int cluster_load_shared(const int* local, unsigned rank) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(local), ra, v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return (int)v;
+}
+
+// Per-block scratch of the per-replica engine.
 struct EnsShared {
+    int maxv, job;
     long long entries;
-    int far, close, maxv, job;
     int carry;
     int warp_tot[32];
 };
@@ -1458,12 +1496,15 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// Exclusive scan of the replica's cell counts into cell_start, block-wide,
+// Exclusive scan of the replica's cell counts into cell_start, by one block,
 // and the largest occupancy (the paper's N_l) into C->max_occ.
 template <class P>
 __device__ __noinline__ void ens_scan(const Args<P>& a, EnsShared& sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) sh.carry = 0;
+    if (threadIdx.x == 0) {
+        sh.carry = 0;
+        sh.maxv = 0;
+    }
     int mx = 0;
     __syncthreads();
     for (int base = 0; base < a.ncells; base += blockDim.x) {
@@ -1492,36 +1533,37 @@ __device__ __noinline__ void ens_scan(const Args<P>& a, EnsShared& sh) {
         if (threadIdx.x == blockDim.x - 1) sh.carry = excl + v;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        a.cell_start[a.ncells] = (int)a.n;
-        sh.maxv = 0;
-        sh.entries = 0;
-    }
-    __syncthreads();
     atomicMax(&sh.maxv, mx);
     __syncthreads();
-    if (threadIdx.x == 0) a.ctr->max_occ = sh.maxv;
+    if (threadIdx.x == 0) {
+        a.cell_start[a.ncells] = (int)a.n;
+        Counters* C = a.ctr;
+        C->max_occ = sh.maxv;
+        C->max_nn = 0;
+        C->list_entries = 0;
+    }
 }
 
 // The rebuild branch of one replica (the kernels k_bin .. k_rebuild_done,
-// block-wide with barriers between the phases).
+// with team barriers between the phases).
 template <class P>
-__device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh) {
+__device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh, Team tm) {
     Counters* C = a.ctr;
-    const int64_t n = a.n, t0 = threadIdx.x, dt = blockDim.x;
+    const int64_t n = a.n, t0 = tm.first(), dt = tm.stride();
     for (int64_t i = t0; i < n; i += dt) bin_item<P>(a, i);
-    __syncthreads();
-    ens_scan<P>(a, sh);
+    tm.sync();
+    if (tm.lead_block()) ens_scan<P>(a, sh);
+    tm.sync();
     for (int64_t t = t0; t < n; t += dt) scatter_item<P>(a, t);
     for (int64_t c = t0; c < a.ncells; c += dt) a.count[c] = 0;
-    __syncthreads();
+    tm.sync();
     for (int64_t c = t0; c < a.ncells; c += dt) cellsort_item<P>(a, c);
-    __syncthreads();
+    tm.sync();
     for (int64_t s = t0; s < n; s += dt) gather_item<P>(a, s);
-    __syncthreads();
+    tm.sync();
     if (C->reorder_now) {
         for (int64_t s = t0; s < n; s += dt) commit_item<P>(a, s);
-        __syncthreads();
+        tm.sync();
     }
     int mx = 0;
     long long sum = 0;
@@ -1530,12 +1572,16 @@ __device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh) {
         mx = max(mx, m);
         sum += m;
     }
-    atomicMax(&sh.maxv, mx);
-    atomicAdd((unsigned long long*)&sh.entries, (unsigned long long)sum);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        C->max_nn = sh.maxv;
-        C->list_entries = sh.entries;
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&C->max_nn, mx);
+        atomicAdd((unsigned long long*)&C->list_entries, (unsigned long long)sum);
+    }
+    tm.sync();
+    if (tm.leader()) {
         C->rebuilds += 1;
         if (C->reorder_now) {
             C->reorders += 1;
@@ -1544,14 +1590,15 @@ __device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh) {
         }
         C->rebuild_flag = 0;
     }
-    __syncthreads();
+    tm.sync();
 }
 
-// One step of one replica (k_step, block-wide): warps take 32 atoms at a
-// time, stage their list rows, compute forces and integrate; then the
-// counters advance as in k_step's last block.  kFinal: the init or last step.
+// One step of one replica (k_step): warps take 32 atoms at a time, stage
+// their list rows, compute forces and integrate; then the counters advance
+// as in k_step's last block.  kFinal: the init or last step, whose KE, PE
+// and W are summed over 32-atom chunks in a fixed order.
 template <class P, bool kFinal>
-__device__ __noinline__ void ens_step(const Args<P>& a, EnsShared& sh, int* rows, bool init) {
+__device__ __noinline__ void ens_step(const Args<P>& a, int* rows, bool init, Team tm) {
     Counters* C = a.ctr;
     const int err = C->error;
     const long long left = C->steps_left;
@@ -1561,15 +1608,10 @@ __device__ __noinline__ void ens_step(const Args<P>& a, EnsShared& sh, int* rows
     const bool energy = init || last;
     const typename P::pos4* pc = par ? a.pB : a.pA;
     typename P::pos4* pn = par ? a.pA : a.pB;
-    if (threadIdx.x == 0) {
-        sh.far = 0;
-        sh.close = 0;
-    }
-    __syncthreads();
     bool far = false, close = false;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t nchunks = (a.n + 31) / 32;
-    for (int64_t ch = threadIdx.x >> 5; ch < nchunks; ch += nw) {
+    for (int64_t ch = (int64_t)tm.rank * nw + (threadIdx.x >> 5); ch < nchunks; ch += (int64_t)tm.size * nw) {
         const int64_t i = ch * 32 + lane;
         int cnt, staged;
         const int* col;
@@ -1595,15 +1637,15 @@ __device__ __noinline__ void ens_step(const Args<P>& a, EnsShared& sh, int* rows
         }
         __syncwarp();  // the next chunk's copies overwrite rows
     }
-    if (__any_sync(0xffffffffu, far) && lane == 0) atomicOr(&sh.far, 1);
-    if (__any_sync(0xffffffffu, close) && lane == 0) atomicOr(&sh.close, 1);
-    __syncthreads();
+    if (__any_sync(0xffffffffu, far) && lane == 0) atomicOr(&C->far_flag, 1u);
+    if (__any_sync(0xffffffffu, close) && lane == 0) atomicOr(&C->close_flag, 1);
+    tm.sync();
     if (kFinal && energy) {
         // chunk sums -> sums of 32 consecutive chunks (fixed shape, in any
         // warp) -> their sum in order: the same numbers whatever the launch
         const int64_t ngroups = (nchunks + 31) / 32;
         double* gsum = a.part + 3 * nchunks;
-        for (int64_t g = threadIdx.x >> 5; g < ngroups; g += nw) {
+        for (int64_t g = (int64_t)tm.rank * nw + (threadIdx.x >> 5); g < ngroups; g += (int64_t)tm.size * nw) {
             const int64_t c = g * 32 + lane;
             double k = c < nchunks ? a.part[3 * c + 0] : 0.0;
             double u = c < nchunks ? a.part[3 * c + 1] : 0.0;
@@ -1619,10 +1661,9 @@ __device__ __noinline__ void ens_step(const Args<P>& a, EnsShared& sh, int* rows
                 gsum[3 * g + 2] = w;
             }
         }
-        __syncthreads();
+        tm.sync();
     }
-    if (threadIdx.x == 0) {
-        if (sh.far) C->far_flag = 1u;
+    if (tm.leader()) {
         if (active && !init) {
             C->steps_left = left - 1;
             C->step += 1;
@@ -1637,10 +1678,13 @@ __device__ __noinline__ void ens_step(const Args<P>& a, EnsShared& sh, int* rows
         } else if (!init) {
             C->far_flag = 0u;
         }
-        if (sh.close) C->error |= kErrClose;
+        if (C->close_flag) {
+            C->error |= kErrClose;
+            C->close_flag = 0;
+        }
         if (kFinal && energy && active) {
-            const int64_t nchunks_ = (a.n + 31) / 32, ngroups = (nchunks_ + 31) / 32;
-            const double* gsum = a.part + 3 * nchunks_;
+            const int64_t ngroups = (nchunks + 31) / 32;
+            const double* gsum = a.part + 3 * nchunks;
             double k = 0.0, u = 0.0, w = 0.0;
             for (int64_t g = 0; g < ngroups; g++) {
                 k += gsum[3 * g + 0];
@@ -1652,78 +1696,101 @@ __device__ __noinline__ void ens_step(const Args<P>& a, EnsShared& sh, int* rows
             C->virial = w;
         }
     }
-    __syncthreads();
+    tm.sync();
 }
 
-// The per-replica engine: each block takes jobs from a queue (jobs are in
-// decreasing order of work) and runs one replica at a time from load to its
-// last step -- md_set_state and md_step for that replica, with block
-// barriers where the single-simulation path has kernel boundaries.
-// Dynamic shared memory: kStageRows x 32 ints per warp.
+// One job: load the replica's state when asked (md_set_state), then
+// `nsteps` steps (md_step).  Every block of the team runs it.
+template <class P>
+__device__ __noinline__ void ens_job(const Args<P>& a, EnsShared& sh, int* rows, int init, long long nsteps,
+                                     Team tm) {
+    Counters* C = a.ctr;
+    if (init) {
+        if (tm.leader()) {
+            Counters z = {};
+            z.rebuild_flag = 1;
+            z.reorder_now = 1;
+            *C = z;
+        }
+        tm.sync();
+        for (int64_t i = tm.first(); i < a.n; i += tm.stride()) set_state_item<P>(a, i);
+        tm.sync();
+        if (C->error == 0) ens_rebuild<P>(a, sh, tm);
+        if (C->error == 0) ens_step<P, true>(a, rows, true, tm);
+    }
+    if (nsteps > 0 && C->error == 0) {
+        bool far = false;
+        const int par = C->parity;
+        for (int64_t i = tm.first(); i < a.n; i += tm.stride()) far |= kickdrift_item<P>(a, i, par ? a.pB : a.pA);
+        if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
+        tm.sync();
+        if (tm.leader()) {
+            C->steps_left = nsteps;
+            decide_rebuild(C, a.cell_list_only, a.reorder_interval);
+        }
+        tm.sync();
+        for (long long st = 0; st < nsteps; st++) {
+            if (C->rebuild_flag) ens_rebuild<P>(a, sh, tm);
+            if (C->error) break;
+            if (st + 1 < nsteps) ens_step<P, false>(a, rows, false, tm);
+            else ens_step<P, true>(a, rows, false, tm);
+            if (C->error) break;
+        }
+    }
+    tm.sync();
+}
+
+template <class P>
+__device__ __forceinline__ void ens_load_args(Args<P>& dst, const Args<P>* src) {
+    static_assert(sizeof(Args<P>) % 16 == 0, "Args must be a whole number of 16-byte words");
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(&dst);
+    for (int k = threadIdx.x; k < (int)(sizeof(Args<P>) / 16); k += blockDim.x) d4[k] = s4[k];
+}
+
+// The per-replica engine.  Jobs [0, nteam) -- the big replicas -- are run
+// by whole clusters (when the launch has clusters of more than one block),
+// taken from queue[0] by each cluster's first block; the remaining jobs are
+// run by single blocks, taken from queue[1].  Both lists are in decreasing
+// order of work.  Dynamic shared memory: kStageRows x 32 ints per warp.
 template <class P>
 __global__ void __launch_bounds__(1024, 1) k_ensemble(const Args<P>* __restrict__ reps, EnsJob* jobs, int njobs,
-                                                       int* next) {
+                                                       int nteam, int* queue) {
     extern __shared__ __align__(16) int ens_rows[];
     __shared__ EnsShared sh;
     __shared__ __align__(16) Args<P> a;
     int* rows = ens_rows + (threadIdx.x >> 5) * (kStageRows * 32);
+    const unsigned cs = cluster_size();
+    if (cs > 1) {
+        const Team tm{(int)cluster_rank(), (int)cs};
+        for (;;) {
+            if (tm.leader()) sh.job = atomicAdd(&queue[0], 1);
+            tm.sync();
+            const int j = cluster_load_shared(&sh.job, 0);
+            tm.sync();  // the first block keeps its slot until everyone has read it
+            if (j >= nteam) break;
+            ens_load_args<P>(a, reps + jobs[j].rep);
+            if (tm.leader()) jobs[j].t_start = globaltimer_ns();
+            tm.sync();
+            ens_job<P>(a, sh, rows, jobs[j].init, jobs[j].nsteps, tm);
+            if (tm.leader()) jobs[j].t_end = globaltimer_ns();
+        }
+    }
+    const Team solo{0, 1};
     for (;;) {
-        if (threadIdx.x == 0) sh.job = atomicAdd(next, 1);
+        if (threadIdx.x == 0) sh.job = nteam + atomicAdd(&queue[1], 1);
         __syncthreads();
         const int j = sh.job;
-        if (j >= njobs) return;
-        {  // the replica's arguments, copied by the whole block in 16-byte words
-            static_assert(sizeof(Args<P>) % 16 == 0, "Args must be a whole number of 16-byte words");
-            const int4* src = reinterpret_cast<const int4*>(reps + jobs[j].rep);
-            int4* dst = reinterpret_cast<int4*>(&a);
-            for (int k = threadIdx.x; k < (int)(sizeof(Args<P>) / 16); k += blockDim.x) dst[k] = src[k];
-        }
+        if (j >= njobs) break;
+        ens_load_args<P>(a, reps + jobs[j].rep);
         if (threadIdx.x == 0) jobs[j].t_start = globaltimer_ns();
         __syncthreads();
-        Counters* C = a.ctr;
-        if (jobs[j].init) {
-            {  // counters of a freshly loaded state: a rebuild with reorder is pending
-                static_assert(sizeof(Counters) % 8 == 0, "Counters must be a whole number of 8-byte words");
-                long long* w = reinterpret_cast<long long*>(C);
-                for (int k = threadIdx.x; k < (int)(sizeof(Counters) / 8); k += blockDim.x) w[k] = 0;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    C->rebuild_flag = 1;
-                    C->reorder_now = 1;
-                }
-            }
-            __syncthreads();
-            for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) set_state_item<P>(a, i);
-            __syncthreads();
-            if (C->error == 0) ens_rebuild<P>(a, sh);
-            if (C->error == 0) ens_step<P, true>(a, sh, rows, true);
-        }
-        const long long nsteps = jobs[j].nsteps;
-        if (nsteps > 0 && C->error == 0) {
-            if (threadIdx.x == 0) sh.far = 0;
-            __syncthreads();
-            bool far = false;
-            const int par = C->parity;
-            for (int64_t i = threadIdx.x; i < a.n; i += blockDim.x) far |= kickdrift_item<P>(a, i, par ? a.pB : a.pA);
-            if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&sh.far, 1);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (sh.far) C->far_flag = 1u;
-                C->steps_left = nsteps;
-                decide_rebuild(C, a.cell_list_only, a.reorder_interval);
-            }
-            __syncthreads();
-            for (long long st = 0; st < nsteps; st++) {
-                if (C->rebuild_flag) ens_rebuild<P>(a, sh);
-                if (C->error) break;
-                if (st + 1 < nsteps) ens_step<P, false>(a, sh, rows, false);
-                else ens_step<P, true>(a, sh, rows, false);
-                if (C->error) break;
-            }
-        }
-        __syncthreads();
+        ens_job<P>(a, sh, rows, jobs[j].init, jobs[j].nsteps, solo);
         if (threadIdx.x == 0) jobs[j].t_end = globaltimer_ns();
         __syncthreads();
+    }
+    if (cs > 1) {  // no block leaves while another of its cluster may still address it
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
 }
 

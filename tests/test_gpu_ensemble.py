@@ -22,11 +22,12 @@ def _state(n, rho, T, seed):
     return state(n, rho, T, seed, jitter=0.05)
 
 
-CASES = [  # (n, rho, T, seed, reorder_interval)
-    (500, 0.8, 1.0, 11, 100),
-    (2048, 0.6, 0.7, 12, 20),
-    (4000, 1.0, 2.0, 13, 0),
-    (6912, 0.8, 1.5, 14, 7),
+CASES = [  # (n, rho, T, seed, reorder_interval, cluster, team_atoms)
+    (500, 0.8, 1.0, 11, 100, 8, 0),
+    (2048, 0.6, 0.7, 12, 20, 1, 0),
+    (4000, 1.0, 2.0, 13, 0, 4, 1000),   # a team of 4 blocks on a small replica
+    (6912, 0.8, 1.5, 14, 7, 2, 1000),
+    (10976, 0.7, 1.0, 15, 30, 8, 0),    # above the default team size
 ]
 
 
@@ -49,11 +50,12 @@ def _ens_run(e, rid, steps):
 
 @pytest.mark.parametrize("case", CASES)
 def test_replica_matches_md_step_bitwise(case):
-    n, rho, T, seed, reorder = case
+    n, rho, T, seed, reorder, cluster, team_atoms = case
     pos, vel, L = _state(n, rho, T, seed)
     steps = [37, 1, 64]
     p0, v0, m0 = _solo(pos, vel, L, steps, reorder)
     with md.Ensemble(ARENA) as e:
+        e.set_shape(1024 if cluster > 1 else 256, 0, cluster, team_atoms)
         rid = e.add(pos, vel, L, RC, 0.4, DT, reorder_interval=reorder)
         p1, v1, m1 = _ens_run(e, rid, steps)
         assert e.status(rid) == md.MD_OK
@@ -99,14 +101,14 @@ def test_result_is_the_same_alone_and_in_the_mix():
     assert alone[2] == mixed[2]  # every field, energies included (fixed summation order)
 
 
-@pytest.mark.parametrize("block", [64, 128, 512, 1024])
-def test_launch_shape_does_not_change_results(block):
-    rng = np.random.default_rng(9)
+@pytest.mark.parametrize("shape", [(64, 0, 1, 0), (128, 0, 1, 0), (512, 7, 1, 0), (1024, 0, 1, 0),
+                                   (1024, 0, 8, 1500), (512, 0, 4, 2500), (256, 16, 2, 1000)])
+def test_launch_shape_does_not_change_results(shape):
     ref = None
-    for b in (256, block):
+    for sh in ((256, 0, 1, 0), shape):
         with md.Ensemble(ARENA) as e:
             ids = _mix(e, np.random.default_rng(9), 6)
-            e.set_shape(b, 0 if b != 512 else 7)
+            e.set_shape(*sh)
             e.run(ids, [40, 80, 120, 10, 0, 60])
             e.sync()
             got = [e.get_state(i) + (e.measure(i),) for i in ids]
@@ -151,10 +153,10 @@ def test_times_and_autotune():
     rng = np.random.default_rng(3)
     with md.Ensemble(ARENA) as e:
         ids = _mix(e, rng, 12)
-        b, g = e.autotune(ids, probe_steps=5)
-        assert b in (128, 256, 512, 1024) and g == 0
+        b, c = e.autotune(ids, probe_steps=5)
+        assert b in (256, 512, 1024) and c in (1, 4, 8)
         e.run(ids, [50] * len(ids))
         t0, t1 = e.times(ids)
         assert np.all(t0 >= 0) and np.all(t1 >= t0)
         for i in ids:
-            assert e.measure(i)["step"] == 4 * 5 + 50
+            assert e.measure(i)["step"] == 5 * 5 + 50
