@@ -10,7 +10,8 @@ new requests overlaps on the device.  A finished request's state is copied
 back and its arena space is freed at the slice boundary where it finishes.
 
 Requests of at least ``big_atoms`` atoms do not go into the ensemble,
-whose engine gives each replica one thread block (one SM): each gets a
+whose engine gives a replica one thread block (one SM), or one cluster of
+eight blocks when it has 8192 atoms or more: each gets a
 single-simulation handle of its own (md_create; device memory counted
 against the same budget) driven by a worker thread, so its grid-wide
 kernels spread over the SMs the ensemble's launch leaves free, on its own
@@ -75,14 +76,19 @@ class Request:
 class Server:
     """Admits requests by arena space, runs them in slices, retires them."""
 
-    def __init__(self, budget_bytes: int, slice_steps: int = 200, big_atoms: int = 16384, arena_fraction=0.5,
-                 max_replicas: int = 4096, device: int = -1, stream=None, keep_results: bool = True):
+    def __init__(self, budget_bytes: int, slice_steps: int = 200, big_atoms: int = 65536, arena_fraction=0.5,
+                 max_replicas: int = 4096, device: int = -1, stream=None, keep_results: bool = True,
+                 slice_atom_steps: int = 2_000_000):
         self.arena_bytes = int(budget_bytes * arena_fraction)
         self.solo_budget = int(budget_bytes) - self.arena_bytes
         self.solo_used = 0
         self.device = device
         self.ens = Ensemble(self.arena_bytes, max_replicas=max_replicas, device=device, stream=stream)
+        # big ensemble members run on clusters of team_blocks 1024-thread blocks
+        self.team_atoms, self.team_blocks = 8192, 8
+        self.ens.set_shape(1024, 0, self.team_blocks, self.team_atoms)
         self.slice_steps = int(slice_steps)
+        self.slice_atom_steps = int(slice_atom_steps)
         self.big_atoms = int(big_atoms)
         self.keep_results = keep_results
         self.queue: list[Request] = []
@@ -183,7 +189,16 @@ class Server:
         if not self.active:
             return False
         ids = list(self.active.keys())
-        steps = [min(self.active[r].left, self.slice_steps) for r in ids]
+        # about the same work per block in one slice: small replicas take
+        # more steps than big ones (at least slice_steps when they can), so
+        # no slice waits long for its largest member
+        steps = []
+        for r in ids:
+            q = self.active[r]
+            k = max(self.slice_steps, self.slice_atom_steps // max(q.atoms, 1))
+            if q.atoms >= self.team_atoms:
+                k = max(1, (self.slice_atom_steps * self.team_blocks) // q.atoms)
+            steps.append(min(q.left, k))
         self.ens.run(ids, steps)
         self.ens.sync()
         with self._lock:
