@@ -162,6 +162,15 @@ int md_create(const double box[3], int64_t n, double rc, double skin, double dt,
 int md_set_state(md_handle* h, const double* pos, const double* vel);
 int md_set_state_device(md_handle* h, const double* pos, const double* vel);
 
+/* Velocity adjustment, Sec. 3.1 step (f) (during equilibration): scales
+ * every velocity by s = sqrt(3 N T / (2 KE)), KE the kinetic energy of the
+ * current state (after the last md_step or md_set_state), so that the
+ * temperature 2 KE / (3 N) becomes T.  Sec. 5's protocol calls it every 20
+ * steps during the first 500.  Each velocity is multiplied in FP64 and
+ * stored in the form's velocity precision; md_measure then reports the new
+ * KE.  MD_EINVAL if T <= 0 or KE is 0; MD_ESTATE before md_set_state. */
+int md_rescale(md_handle* h, double T);
+
 /* Advances nsteps velocity-Verlet steps (Sec. 3.1 (a)-(e)).  The neighbour
  * list is rebuilt on the device whenever the largest displacement since the
  * last build reaches skin/2 (every step in cell-list-only mode); atoms are

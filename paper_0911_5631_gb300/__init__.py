@@ -133,6 +133,7 @@ SIGNATURES = [
                             C.POINTER(_H)]),
     ("md_set_state", C.c_int, [_H, C.c_void_p, C.c_void_p]),
     ("md_set_state_device", C.c_int, [_H, C.c_void_p, C.c_void_p]),
+    ("md_rescale", C.c_int, [_H, C.c_double]),
     ("md_step", C.c_int, [_H, C.c_int64]),
     ("md_measure", C.c_int, [_H, C.POINTER(md_measure_t)]),
     ("md_get_state", C.c_int, [_H, C.c_void_p, C.c_void_p]),
@@ -249,6 +250,10 @@ def md_set_state(h, pos, vel, n):
 
 def md_set_state_device(h, pos_ptr: int, vel_ptr: int):
     return _check(lib().md_set_state_device(h, C.c_void_p(pos_ptr), C.c_void_p(vel_ptr)), h)
+
+
+def md_rescale(h, T):
+    return _check(lib().md_rescale(h, float(T)), h)
 
 
 def md_step(h, nsteps):
@@ -384,6 +389,9 @@ class Simulation:
             md_set_state_device(self.h, pos.data_ptr(), vel.data_ptr())
         else:
             md_set_state(self.h, pos, vel, self.n)
+
+    def rescale(self, T):
+        md_rescale(self.h, T)
 
     def step(self, nsteps):
         md_step(self.h, nsteps)

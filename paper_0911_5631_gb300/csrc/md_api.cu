@@ -54,6 +54,7 @@ struct SimBase {
     virtual ~SimBase() {}
     virtual int set_state(const double* pos, const double* vel, bool device) = 0;
     virtual int step(int64_t n) = 0;
+    virtual int rescale(double T) = 0;
     virtual int measure(md_measure_t* out) = 0;
     virtual int get_state(double* pos, double* vel, bool device) = 0;
     virtual int get_forces(double* f) = 0;
@@ -542,6 +543,29 @@ struct Sim : SimBase {
         return MD_OK;
     }
 
+    int rescale(double T) override {
+        DevGuard dg(device);
+        if (!have_state) {
+            err = "md_rescale before md_set_state";
+            return MD_ESTATE;
+        }
+        if (!(T > 0.0) || !std::isfinite(T)) {
+            err = "T must be positive and finite";
+            return MD_EINVAL;
+        }
+        MD_CUDA(launch(kt.finalize, 1, kBlock, a));
+        Counters c;
+        int r = read_counters(&c);
+        if (r) return r;
+        if (!(c.ke > 0.0)) {
+            err = "kinetic energy is zero";
+            return MD_EINVAL;
+        }
+        double s = std::sqrt(1.5 * (double)a.n * T / c.ke);
+        MD_CUDA(launch(kt.rescale, grid_atoms(), kBlock, a, s));
+        return MD_OK;
+    }
+
     int measure(md_measure_t* out) override {
         DevGuard dg(device);
         if (!out) {
@@ -799,6 +823,10 @@ int md_set_state_device(md_handle* h, const double* pos, const double* vel) {
 int md_step(md_handle* h, int64_t nsteps) {
     MD_HANDLE_CHECK(h);
     return h->sim->step(nsteps);
+}
+int md_rescale(md_handle* h, double T) {
+    MD_HANDLE_CHECK(h);
+    return h->sim->rescale(T);
 }
 int md_measure(md_handle* h, md_measure_t* out) {
     MD_HANDLE_CHECK(h);

@@ -1339,6 +1339,36 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
     }
 }
 
+// Step (f) of Sec. 3.1: v <- s v (the product in FP64, stored in the
+// velocity precision), and this block's KE partial of the new velocities
+// (PE and W partials are those of the last final step and stay).
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_rescale(Args<P> a, double s) {
+    __shared__ double shs[kBlock / 32];
+    using vel = typename P::vel;
+    const int64_t i = gtid();
+    double ke = 0.0;
+    if (i < a.n) {
+        vel* v[3] = {a.vx, a.vy, a.vz};
+        for (int d = 0; d < 3; d++) {
+            double x;
+            if constexpr (P::kFp64) x = v[d][i] * s;
+            else x = cvt::f64(v[d][i]) * s;
+            vel y;
+            if constexpr (P::kFp64) y = x;
+            else y = cvt::f32(x);
+            v[d][i] = y;
+            double dy;
+            if constexpr (P::kFp64) dy = y;
+            else dy = cvt::f64(y);
+            ke += dy * dy;
+        }
+        ke *= 0.5;
+    }
+    const double bk = block_sum(ke, shs);
+    if (threadIdx.x == 0) a.part[3 * blockIdx.x + 0] = bk;
+}
+
 // Sums the per-block partials of the last init/final step in a fixed order.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_finalize(Args<P> a) {
@@ -1825,6 +1855,7 @@ KernelTable<P> make_kernel_table() {
     t.reset_counters = (void*)k_reset_counters<P>;
     t.clear_overflow = (void*)k_clear_overflow<P>;
     t.selftest = (void*)k_selftest<P>;
+    t.rescale = (void*)k_rescale<P>;
     if constexpr (!P::kFp64) t.ensemble = (void*)k_ensemble<P>;
     else t.ensemble = nullptr;
     return t;

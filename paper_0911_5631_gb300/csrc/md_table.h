@@ -31,6 +31,7 @@ struct KernelTable {
     void* reset_counters;
     void* clear_overflow;
     void* selftest;
+    void* rescale;
     void* ensemble;  // mixed form only (nullptr for FP64)
 };
 

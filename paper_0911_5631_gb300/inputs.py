@@ -112,6 +112,25 @@ def wca_state(n: int, rho: float, T: float, seed: int, jitter_amp: float = 0.0,
     return pos, vel, L
 
 
+def sc_state(n_e: int, rho: float, T: float, seed: int):
+    """(pos, vel, L): the initial state the paper describes -- atoms on a
+    simple cubic lattice of edge n_e (n_e^3 atoms, sites (i + 1/2) a - L/2),
+    velocities of magnitude sqrt(3 T) in uniformly random directions, then
+    the centre-of-mass velocity subtracted."""
+    L = box_for(n_e ** 3, rho)
+    a = L / n_e
+    g = (np.arange(n_e) + 0.5)
+    z, y, x = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([x.ravel() * a[0], y.ravel() * a[1], z.ravel() * a[2]], axis=1) - L / 2
+    u = uniform(seed, 2 * n_e ** 3).reshape(-1, 2)
+    cz = 2.0 * u[:, 0] - 1.0
+    phi = 2.0 * np.pi * u[:, 1]
+    sz = np.sqrt(np.maximum(0.0, 1.0 - cz * cz))
+    vel = np.sqrt(3.0 * T) * np.stack([sz * np.cos(phi), sz * np.sin(phi), cz], axis=1)
+    vel -= vel.mean(axis=0)
+    return pos, vel, L
+
+
 # Workloads of the soft-sphere benchmark suite, by size and thermodynamic
 # state.  rc = 2^(1/6) throughout, dt = 0.005.
 WCA_RC = 2.0 ** (1.0 / 6.0)

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+import paper_0911_5631_gb300 as md
 from mdcheck import (DT, FORCE_TOL, RC, assert_same_pairs, ensure_built, min_image, oracle_grid,
                      rel_rms, sim, state)
 
@@ -191,3 +192,33 @@ def test_tiny_systems():
         assert f[1, 0] == pytest.approx(-fr * 0.9, rel=FORCE_TOL[prec] * 10)
         assert s.measure()["pe"] == pytest.approx(u, rel=1e-6)
         s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_rescaled_equilibration_segment(prec):
+    # step (f): velocities rescaled to T every 20 steps, as the oracle does
+    # after its step 20, 40, ..., 100
+    k, every, T = 100, 20, 1.3
+    pos, vel, L, skin = _fluid(CASES[0])
+    s = sim(pos, vel, L, skin=skin, precision=prec)
+    ref = oracle.run(pos, vel, L, RC, skin, DT, k, rescale_every=every, rescale_until=k, T_target=T)
+    for _ in range(k // every):
+        s.step(every)
+        s.rescale(T)
+        assert 2.0 * s.measure()["ke"] / (3.0 * pos.shape[0]) == pytest.approx(T, rel=1e-6)
+    p, v = s.get_state()
+    f_rms = float(np.sqrt(np.mean(ref["f"] ** 2)))
+    dv, dx = _trajectory_tol(prec, f_rms, k)
+    assert np.sqrt(np.mean((v - ref["vel"]) ** 2)) <= dv
+    assert np.sqrt(np.mean(min_image(p - ref["pos"], L) ** 2)) <= dx
+    s.close()
+
+
+def test_rescale_rejects_bad_temperature():
+    pos, vel, L, skin = _fluid(CASES[1])
+    s = sim(pos, vel, L, skin=skin)
+    for T in (0.0, -1.0, float("nan")):
+        with pytest.raises(md.MDError) as e:
+            s.rescale(T)
+        assert e.value.code == md.MD_EINVAL
+    s.close()
