@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--ens-replicas", type=int, default=inputs.ENSEMBLE["replicas"])
     ap.add_argument("--ens-steps", type=int, default=inputs.ENSEMBLE["steps"])
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace lines")
+    ap.add_argument("--no-lj", action="store_true", help="skip the Lennard-Jones line")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-low-rate", type=float, default=10.0,
                     help="arrival rate of the second, below-saturation trace")
@@ -288,6 +289,39 @@ def serving_bench(md, stream, device, count, rate, budget_bytes, slice_steps):
     return st
 
 
+def lj_bench(md, torch, stream, device, steps, chunk=100):
+    """The Lennard-Jones workload (r_c = 3, rho 0.38, T 1.2, shell 0.8, 1M
+    atoms, mixed form): atom-steps/s over `steps` benchmark steps of `chunk`
+    MD steps after 200 untimed steps."""
+    cfg = inputs.WORKLOADS["lj_fcc64_n1m_rc3"]
+    n = cfg["n"]
+    pos, vel, L = inputs.wca_state(n, cfg["rho"], cfg["T"], cfg["seed"])
+    s = md.Simulation(L, n, cfg["rc"], cfg["skin"], DT, precision="mixed", reorder_interval=100,
+                      stream=stream.cuda_stream, device=device)
+    try:
+        s.set_state(pos, vel)
+        s.step(200)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        m0 = s.measure()
+        e0.record(stream)
+        for _ in range(steps):
+            s.step(chunk)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        m1 = s.measure()
+        if m1["step"] - m0["step"] != steps * chunk:
+            raise RuntimeError("LJ run advanced %d steps" % (m1["step"] - m0["step"]))
+        return {"workload": "lj_fcc64_n1m_rc3", "n_atoms": n, "rho": cfg["rho"], "T": cfg["T"], "rc": cfg["rc"],
+                "skin": cfg["skin"], "value": n * steps * chunk / (ms / 1e3), "unit": UNIT,
+                "ms_per_md_step": ms / (steps * chunk), "neighbours_per_atom": m1["list_entries"] / n,
+                "rebuilds": m1["rebuilds"] - m0["rebuilds"], "md_steps": steps * chunk}
+    finally:
+        s.close()
+
+
 def run_ours(args):
     import torch
     import paper_0911_5631_gb300 as md
@@ -430,6 +464,9 @@ def run_ours(args):
     ens = None
     if rank == 0 and not args.no_ensemble:
         ens = ensemble_bench(md, torch, stream, local, args.ens_replicas, args.ens_steps, 10)
+    lj = None
+    if rank == 0 and not args.no_lj:
+        lj = lj_bench(md, torch, stream, local, 5)
     serving = None
     if rank == 0 and not args.no_serving:
         serving = [serving_bench(md, stream, local, args.serve_requests, rate, 40 << 30, 200)
@@ -455,6 +492,7 @@ def run_ours(args):
             "fp64_form": fp64,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "lj": lj,
             "ensemble": ens,
             "serving": serving,
             "clocks": clk,
