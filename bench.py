@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--ens-steps", type=int, default=inputs.ENSEMBLE["steps"])
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace lines")
     ap.add_argument("--no-lj", action="store_true", help="skip the Lennard-Jones line")
+    ap.add_argument("--ablations", action="store_true", help="add the reorder-interval ablation")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-low-rate", type=float, default=10.0,
                     help="arrival rate of the second, below-saturation trace")
@@ -322,6 +323,40 @@ def lj_bench(md, torch, stream, device, steps, chunk=100):
         s.close()
 
 
+def ablations(md, torch, stream, device, pos, vel, L, cfg, chunk=100, steps=5):
+    """The paper's ablations on the 1M workload (mixed form): the reorder
+    interval (Tables 7, 8; 0 = never after the load) -- atom-steps/s and the
+    step kernel's time, each from an equilibrated state."""
+    out = []
+    for interval in (0, 20, 100, 500):
+        s = md.Simulation(L, cfg["n"], RC, cfg["skin"], DT, precision="mixed", reorder_interval=interval,
+                          stream=stream.cuda_stream, device=device)
+        try:
+            s.set_state(pos, vel)
+            s.step(1000)  # long enough for the storage order to drift from the cell order
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                s.step(chunk)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            s.set_profiling(True)
+            k0 = s.kernel_stats()
+            s.step(chunk)
+            k1 = s.kernel_stats()
+            s.set_profiling(False)
+            kl = k1["step_kernel_launches"] - k0["step_kernel_launches"]
+            out.append({"reorder_interval": interval, "value": cfg["n"] * chunk * steps / (ms / 1e3), "unit": UNIT,
+                        "step_kernel_us": 1e3 * (k1["step_kernel_ms"] - k0["step_kernel_ms"]) / max(kl, 1),
+                        "reorders": s.measure()["reorders"]})
+        finally:
+            s.close()
+    return out
+
+
 def run_ours(args):
     import torch
     import paper_0911_5631_gb300 as md
@@ -464,6 +499,9 @@ def run_ours(args):
     ens = None
     if rank == 0 and not args.no_ensemble:
         ens = ensemble_bench(md, torch, stream, local, args.ens_replicas, args.ens_steps, 10)
+    abl = None
+    if rank == 0 and args.ablations:
+        abl = ablations(md, torch, stream, local, eq_pos, eq_vel, L, cfg)
     lj = None
     if rank == 0 and not args.no_lj:
         lj = lj_bench(md, torch, stream, local, 5)
@@ -493,6 +531,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "lj": lj,
+            "ablations": abl,
             "ensemble": ens,
             "serving": serving,
             "clocks": clk,

@@ -68,3 +68,33 @@ def test_eight_million_atoms(rho, T):
     assert m["step"] == 60
     _sampled_force_check(s, L, "mixed", nsample=24)
     s.close()
+
+
+@pytest.mark.parametrize("rho,T", [(1.0, 2.0), (0.6, 0.7)])
+def test_eight_million_energy_drift_and_oracle_segment(rho, T):
+    # 8,388,608 atoms (FCC 128^3 x 4), mixed form: total energy per atom over
+    # 10^4 steps after 500 steps of melting drifts by less than 1e-4; then an
+    # FP64 oracle segment of 5 steps from the GPU's state agrees with the GPU's
+    # own 5 steps within the trajectory tolerance
+    n = 8388608
+    pos, vel, L = state(n, rho, T, 3)
+    s = sim(pos, vel, L, skin=0.4, precision="mixed", reorder_interval=100)
+    s.step(500)
+    e0 = s.measure()["e_tot_per_atom"]
+    for _ in range(10):
+        s.step(1000)
+    m = s.measure()
+    assert m["step"] == 10500
+    assert abs(m["e_tot_per_atom"] - e0) < 1e-4
+    p, v = s.get_state()
+    k = 5
+    ref = oracle.run(p, v, L, RC, 0.4, DT, k, record=False)
+    s.step(k)
+    p2, v2 = s.get_state()
+    s.close()
+    f_rms = float(np.sqrt(np.mean(ref["f"] ** 2)))
+    dv = 10.0 * k * DT * FORCE_TOL["mixed"] * f_rms + 1e-7
+    assert np.sqrt(np.mean((v2 - ref["vel"]) ** 2)) <= dv
+    d = p2 - ref["pos"]
+    d -= np.asarray(L) * np.round(d / np.asarray(L))
+    assert np.sqrt(np.mean(d ** 2)) <= k * DT * dv + 1e-12
