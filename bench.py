@@ -252,7 +252,7 @@ def ensemble_bench(md, torch, stream, device, replicas, steps, probe):
         if bad:
             raise RuntimeError("ensemble replicas failed: %s" % bad[:8])
         m = e.measure(ids[0])
-        if m["step"] != steps + 5 * probe:
+        if m["step"] != steps + 6 * probe:
             raise RuntimeError("ensemble replica advanced %d steps" % m["step"])
         return {"workload": "wca_ensemble_%d" % replicas, "replicas": replicas, "atoms": int(atoms),
                 "n_range": [inputs.ENSEMBLE["n_min"], inputs.ENSEMBLE["n_max"]], "steps": steps,

@@ -347,10 +347,11 @@ int md_ensemble_times(md_ensemble* e, int32_t count, const int32_t* ids, double*
  * limited to one SM; cluster 1 gives every replica one block. */
 int md_ensemble_set_shape(md_ensemble* e, int32_t block, int32_t grid, int32_t cluster, int64_t team_atoms);
 
-/* Autotuner: runs ids for probe_steps steps under each candidate
- * (threads per block, cluster) pair (these are real steps: the replicas
- * advance by probe_steps x number of candidates, 5), keeps the fastest
- * and returns it in *block, *cluster (either may be NULL). */
+/* Autotuner: runs ids for probe_steps steps under each of 6 candidate
+ * shapes -- (threads per block, cluster size, team_atoms) -- (these are
+ * real steps: the replicas advance by 6 x probe_steps), keeps the fastest
+ * and returns its block and cluster size in *block, *cluster (either may
+ * be NULL). */
 int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int64_t probe_steps,
                          int32_t* block, int32_t* cluster);
 

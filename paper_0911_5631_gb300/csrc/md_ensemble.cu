@@ -676,16 +676,21 @@ int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int6
         }
     }
     std::vector<int64_t> steps(count, probe_steps);
-    // candidate shapes: (threads per block, blocks per team of a big replica)
-    const int cands[][2] = {{256, 1}, {1024, 1}, {1024, 4}, {1024, 8}, {512, 8}};
+    // candidate shapes: (threads per block, blocks per team, atoms from which
+    // a replica gets a team)
+    const int cands[][3] = {{256, 1, 0}, {1024, 1, 0}, {1024, 2, 8192}, {1024, 4, 8192},
+                            {1024, 4, 16384}, {1024, 8, 16384}};
+    const int64_t saved_team = e->team_atoms;
     float best = -1.f;
     int best_b = e->block, best_c = e->cluster;
+    int64_t best_t = e->team_atoms;
     cudaEvent_t t0, t1;
     ENS_CUDA(cudaEventCreate(&t0));
     ENS_CUDA(cudaEventCreate(&t1));
     int r = MD_OK;
     for (auto& c : cands) {
         std::vector<EnsJob> jobs;
+        e->team_atoms = c[2] > 0 ? c[2] : saved_team;
         r = make_jobs(e, count, ids, steps.data(), &jobs, c[1], &nteam);
         if (r) break;
         if (cudaEventRecord(t0, e->stream) != cudaSuccess) { r = MD_ECUDA; break; }
@@ -701,6 +706,7 @@ int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int6
             best = ms;
             best_b = c[0];
             best_c = c[1];
+            best_t = e->team_atoms;
         }
     }
     cudaEventDestroy(t0);
@@ -712,6 +718,7 @@ int md_ensemble_autotune(md_ensemble* e, int32_t count, const int32_t* ids, int6
     e->block = best_b;
     e->grid = 0;
     e->cluster = best_c;
+    e->team_atoms = r ? saved_team : best_t;
     if (block) *block = best_b;
     if (cluster) *cluster = best_c;
     return MD_OK;
