@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <climits>
+
 #include "md_common.cuh"
 #include "md_table.h"
 
@@ -894,7 +896,30 @@ __global__ void __launch_bounds__(kBlock) k_scatter(Args<P> a, int guard) {
 // Makes the order inside each cell deterministic (ascending storage index).
 template <class P>
 __device__ __forceinline__ void cellsort_item(const Args<P>& a, int64_t c) {
-    int beg = a.cell_start[c], end = a.cell_start[c + 1];
+    constexpr int kLocal = 8;  // cells this full are sorted in registers
+    const int beg = a.cell_start[c], end = a.cell_start[c + 1];
+    const int len = end - beg;
+    if (len <= 1) return;
+    if (len <= kLocal) {
+        // all loads first (independent), then a sorting network of
+        // compare-exchanges on registers, then all stores
+        int k[kLocal];
+#pragma unroll
+        for (int u = 0; u < kLocal; u++) k[u] = u < len ? a.order[beg + u] : INT_MAX;
+#pragma unroll
+        for (int r = 0; r < kLocal; r++) {  // odd-even transposition sort
+#pragma unroll
+            for (int u = r & 1; u + 1 < kLocal; u += 2) {
+                const int lo = min(k[u], k[u + 1]), hi = max(k[u], k[u + 1]);
+                k[u] = lo;
+                k[u + 1] = hi;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kLocal; u++)
+            if (u < len) a.order[beg + u] = k[u];
+        return;
+    }
     for (int s = beg + 1; s < end; s++) {
         int key = a.order[s];
         int t = s - 1;

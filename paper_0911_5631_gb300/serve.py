@@ -11,7 +11,7 @@ back and its arena space is freed at the slice boundary where it finishes.
 
 Requests of at least ``big_atoms`` atoms do not go into the ensemble,
 whose engine gives a replica one thread block (one SM), or one cluster of
-two blocks when it has 8192 atoms or more: each gets a
+eight blocks when it has 8192 atoms or more: each gets a
 single-simulation handle of its own (md_create; device memory counted
 against the same budget) driven by a worker thread, so its grid-wide
 kernels spread over the SMs the ensemble's launch leaves free, on its own
@@ -85,7 +85,7 @@ class Server:
         self.device = device
         self.ens = Ensemble(self.arena_bytes, max_replicas=max_replicas, device=device, stream=stream)
         # big ensemble members run on clusters of team_blocks 1024-thread blocks
-        self.team_atoms, self.team_blocks = 8192, 2
+        self.team_atoms, self.team_blocks = 8192, 8
         self.ens.set_shape(1024, 0, self.team_blocks, self.team_atoms)
         self.slice_steps = int(slice_steps)
         self.slice_atom_steps = int(slice_atom_steps)
