@@ -160,3 +160,59 @@ def test_times_and_autotune():
         assert np.all(t0 >= 0) and np.all(t1 >= t0)
         for i in ids:
             assert e.measure(i)["step"] == 6 * 5 + 50
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 257])
+def test_tiny_and_ragged_replicas(n):
+    # fewer atoms than a warp, ragged tails, one atom alone in its box
+    L = np.array([7.0, 7.5, 8.0])
+    rng = np.random.default_rng(n)
+    pos = rng.uniform(-L / 2, L / 2, size=(n, 3))
+    if n > 1:  # keep the random start free of overlaps: a coarse lattice
+        g = np.stack(np.meshgrid(*[np.arange(7)] * 3, indexing="ij"), -1).reshape(-1, 3)[:n]
+        pos = (g + 0.5) * (L / 7) - L / 2
+    vel = rng.normal(size=(n, 3))
+    s = sim(pos, vel, L, skin=0.4, precision="mixed")
+    s.step(50)
+    p0, v0 = s.get_state()
+    m0 = s.measure()
+    s.close()
+    with md.Ensemble(ARENA) as e:
+        rid = e.add(pos, vel, L)
+        e.run([rid], [50])
+        e.sync()
+        p1, v1 = e.get_state(rid)
+        m1 = e.measure(rid)
+    assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
+    assert m0["step"] == m1["step"] == 50
+
+
+def test_load_only_run_measures_the_initial_state():
+    pos, vel, L = _state(1500, 0.8, 1.0, 51)
+    s = sim(pos, vel, L, skin=0.4, precision="mixed")
+    m0 = s.measure()
+    s.close()
+    with md.Ensemble(ARENA) as e:
+        rid = e.add(pos, vel, L)
+        with pytest.raises(md.MDError) as err:
+            e.measure(rid)  # not loaded yet
+        assert err.value.code == md.MD_ESTATE
+        e.run([rid], [0])
+        m1 = e.measure(rid)
+    assert m1["step"] == 0
+    for k in ("ke", "pe", "virial"):
+        assert m1[k] == pytest.approx(m0[k], rel=1e-12, abs=1e-12)
+
+
+def test_bad_ids_are_rejected():
+    pos, vel, L = _state(500, 0.8, 1.0, 52)
+    with md.Ensemble(ARENA) as e:
+        rid = e.add(pos, vel, L)
+        for ids, steps in (([rid, rid], [1, 1]), ([rid + 7], [1]), ([rid], [-1])):
+            with pytest.raises(md.MDError) as err:
+                e.run(ids, steps)
+            assert err.value.code == md.MD_EINVAL
+        e.remove(rid)
+        assert e.status(rid) == md.MD_EINVAL  # a removed id is unknown
+        with pytest.raises(md.MDError):
+            e.measure(rid)
