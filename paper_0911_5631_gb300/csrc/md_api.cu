@@ -189,15 +189,17 @@ struct Sim : SimBase {
         chk(alloc(&a.s_vx, n)); chk(alloc(&a.s_vy, n)); chk(alloc(&a.s_vz, n));
         chk(alloc(&a.count, a.ncells)); chk(alloc(&a.cell_start, (size_t)a.ncells + 1));
         chk(alloc(&a.order, n)); chk(alloc(&a.tile_sum, a.ntiles));
-        chk(alloc(&a.nn, n));
+        chk(alloc(&a.nn, n)); chk(alloc(&a.lim, (size_t)(kShellBins - 1) * n));
         chk(alloc(&a.part, (size_t)3 * a.nblocks));
         chk(alloc(&a.ctr, 1));
+        chk(alloc(&a.d2b, (size_t)kD2Buckets * 32));
         chk(alloc(&a.io_pos, (size_t)3 * n)); chk(alloc(&a.io_vel, (size_t)3 * n));
         if (r) return r;
         r = alloc_nbr(a.cap);
         if (r) return r;
         MD_CUDA(cudaMemsetAsync(a.count, 0, sizeof(int) * a.ncells, stream));
         MD_CUDA(cudaMemsetAsync(a.ctr, 0, sizeof(Counters), stream));
+        MD_CUDA(cudaMemsetAsync(a.d2b, 0, sizeof(unsigned) * kD2Buckets * 32, stream));
         MD_CUDA(cudaMemsetAsync(a.nn, 0, sizeof(int) * n, stream));
         MD_CUDA(cudaStreamSynchronize(stream));
         return MD_OK;
@@ -397,7 +399,10 @@ struct Sim : SimBase {
                 int r = flag ? rebuild_eager(0) : MD_OK;
                 if (r) return r;
                 if (profiling && flag) MD_CUDA(cudaEventRecord(ev[4 * s + 3], stream));
-                if (profiling) MD_CUDA(cudaEventRecord(ev[4 * s], stream));
+                if (profiling) {  // entries the step will read, outside its events
+                    MD_CUDA(launch(kt.count_reads, grid_atoms(), kBlock, a));
+                    MD_CUDA(cudaEventRecord(ev[4 * s], stream));
+                }
                 r = step_kernel_eager(kModeAuto, s + 1 == nsteps);
                 if (r) return r;
                 if (profiling) MD_CUDA(cudaEventRecord(ev[4 * s + 1], stream));
@@ -415,6 +420,13 @@ struct Sim : SimBase {
                     }
                 }
                 step_launches += nsteps;
+                // algorithmic bytes: the per-atom state and the entries read
+                Counters c;
+                int rr = read_counters(&c);
+                if (rr) return rr;
+                MD_CUDA(cudaMemsetAsync(&a.ctr->list_reads, 0, sizeof(long long), stream));
+                const int64_t base = (P::kFp64 ? 188 : 120) + (prm.cell_list_only ? 0 : 1);
+                step_bytes += nsteps * base * a.n + 4 * c.list_reads;
             }
         }
         steps_run += nsteps;
@@ -724,8 +736,7 @@ struct Sim : SimBase {
         out->step_kernel_launches = step_launches;
         out->step_kernel_ms = step_ms;
         out->step_kernel_atoms = step_launches * a.n;
-        int64_t base = P::kFp64 ? 188 : 120;
-        out->step_kernel_bytes = step_launches * (base * a.n + 4 * c.list_entries);
+        out->step_kernel_bytes = step_bytes;
         out->rebuilds_timed = rebuilds_timed;
         out->rebuild_ms = rebuild_ms;
         return MD_OK;

@@ -10,6 +10,22 @@ namespace md {
 // Threads per block for every per-atom / per-slot kernel.
 constexpr int kBlock = 256;
 constexpr int kStageRows = 12;  // neighbour-list rows a step-kernel warp copies to shared memory
+// The skin shell [r_c, r_n) is cut into kShellBins bins of width skin /
+// kShellBins.  The build sorts each atom's entries by the bin of their
+// distance at the build and records, for k = 1 .. kShellBins, how many
+// entries lie below r_c + k skin / kShellBins; a step then reads only the
+// entries that the displacements since the build can have brought inside
+// r_c.  The build sorts up to kBuildStage entries per atom in shared memory.
+constexpr int kShellBins = 8;
+constexpr int kBuildStage = 16;
+// The grid kernels keep the running maximum of the squared displacement in
+// kD2Buckets words, one per 128-byte line (block b uses word b mod
+// kD2Buckets), so that the atomics of the many warps of a launch do not
+// queue at one address.
+constexpr int kD2Buckets = 64;
+// Dynamic shared memory of the ensemble engine, ints per thread: the larger
+// of the step's staged rows and the build's staging (entries and distances).
+constexpr int kEnsSmemInts = kStageRows > 2 * kBuildStage ? kStageRows : 2 * kBuildStage;
 // Elements per block of the cell-count scan (kBlock threads x 8).
 constexpr int kScanTile = 2048;
 // Largest neighbour capacity of the mixed form (its fixed-point partial
@@ -53,12 +69,16 @@ struct Counters {
     unsigned int ticket;       // last-block-done counter (reset by the last block)
     unsigned int far_flag;     // some atom moved skin/2 since the last build
     int close_flag;            // a pair came too close during the running step
+    unsigned int d2max;        // bits of the largest squared displacement (FP32, >= 0)
+                               // seen since the last build: a running maximum
+    int reach;                 // shell reach of the next step (1..kShellBins)
     long long steps_left;      // steps still to run in the current md_step
     long long step;            // steps completed since the state was loaded
     long long since_reorder;   // steps since the last reorder
     long long rebuilds;        // rebuilds since the state was loaded
     long long reorders;        // reorders since the state was loaded
     long long list_entries;    // neighbour-list length at the last build
+    long long list_reads;      // entries the profiled steps read (k_count_reads)
     // reduced measurement of the last finalize
     double ke, pe, virial;
 };
@@ -120,6 +140,9 @@ struct alignas(16) Args {
     float thr2f;
     float close2f;      // pairs closer than this flag kErrClose
     float fix_small_fr; // mixed form: a pair with f/r below this has every force component under 2^11
+    float rcf;          // r_c
+    float shell_inv;    // kShellBins / skin (0 without a skin)
+    float shell_eps;    // rounding margin of the shell-bin bound (distance units)
     double close2;
 
     // per-atom state, storage order
@@ -148,6 +171,10 @@ struct alignas(16) Args {
     // neighbour list: entry m of atom i at ((i / 32) * cap + m) * 32 + i % 32
     int* nbr;
     int* nn;            // [n] entries per atom
+    unsigned char* lim; // [kShellBins - 1][n] entries to read at shell reach k = 1..7 in
+                        // plane k - 1; 255 = all (nn)
+    unsigned* d2b;      // [kD2Buckets * 32] running maxima (grid kernels; word 32 b);
+                        // null: ctr->d2max alone (the ensemble engine)
 
     double* part;       // [3 * nblocks] per-block KE, PE, W
     Counters* ctr;

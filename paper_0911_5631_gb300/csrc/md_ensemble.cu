@@ -129,7 +129,7 @@ int64_t lay_out(A& a, const md_plan_t& plan, char* base) {
     at(a.s_vx, n); at(a.s_vy, n); at(a.s_vz, n);
     at(a.count, nc); at(a.cell_start, nc + 1);
     at(a.order, n); at(a.tile_sum, 1);
-    at(a.nn, n);
+    at(a.nn, n); at(a.lim, (kShellBins - 1) * n);
     at(a.nbr, (n + 31) / 32 * 32 * (int64_t)(a.cap > 0 ? a.cap : 1));
     {  // per-chunk (32 atoms) and per-group (32 chunks) energy partials
         const int64_t nch = (n + 31) / 32;
@@ -259,7 +259,7 @@ int launch_run(md_ensemble* e, const std::vector<EnsJob>& jobs, int nteam, int b
     ENS_CUDA(cudaMemsetAsync(e->d_next, 0, 2 * sizeof(int), e->stream));
     int nj = (int)jobs.size();
     if (nteam == 0) cluster = 1;
-    size_t smem = (size_t)(block / 32) * kStageRows * 32 * sizeof(int);
+    size_t smem = (size_t)block * kEnsSmemInts * sizeof(int);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.blockDim = dim3(block);
@@ -413,9 +413,9 @@ int md_ensemble_create(int64_t arena_bytes, int32_t max_replicas, int32_t device
         return fail(MD_ENOMEM);
     }
     e->max_replicas = max_replicas;
-    // the engine's staged rows need more than the default 48 KB of dynamic
-    // shared memory at 1024 threads
-    int smax = 32 * kStageRows * 32 * (int)sizeof(int);
+    // the engine's staged rows and build staging need more than the default
+    // 48 KB of dynamic shared memory at 1024 threads
+    int smax = 1024 * kEnsSmemInts * (int)sizeof(int);
     if (cudaFuncSetAttribute(e->kt.ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize, smax) != cudaSuccess) {
         cudaGetLastError();
         e->err = "cudaFuncSetAttribute failed";

@@ -79,10 +79,10 @@ inline int resolve_plan(const double box[3], int64_t n, double rc, double skin, 
     int64_t per_atom = 3 * 4 /*cell perm rank*/ + 3 * real_b /*pb*/ + 24 /*o*/ + 3 * real_b /*v*/ +
                        3 * real_b /*f*/ + 2 * pos4_b /*pA pB*/ + 16 /*cand*/ + 8 + 3 * real_b + 24 +
                        3 * real_b /*scratch*/ +
-                       4 /*order*/ + 4 /*nn*/ + 48 /*io*/;
+                       4 /*order*/ + 4 /*nn*/ + (kShellBins - 1) /*lim*/ + 48 /*io*/;
     int64_t ncol = (n + 31) / 32 * 32;
     out->device_bytes = per_atom * n + ncol * cap * 4 + (2 * nc + 1) * 4 + ((nc + kScanTile - 1) / kScanTile) * 4 +
-                        3 * nb * 8 + (int64_t)sizeof(Counters);
+                        3 * nb * 8 + (int64_t)sizeof(Counters) + kD2Buckets * 32 * 4;
     return MD_OK;
 }
 
@@ -128,6 +128,12 @@ void fill_args_scalars(Args<P>& a, const md_plan_t& plan, const double box[3], i
     // |f_d| = (f/r) |d_d| < (f/r) r_c for an interacting pair; 2000 leaves
     // room for the rounding of the product below 2^11
     a.fix_small_fr = (float)(2000.0 / std::sqrt(a.rc2));
+    // shell bins: k skin / kShellBins above r_c.  The margin covers the FP32
+    // rounding of the build distances, of the displacement bound and of the
+    // step's distance test (each a few units of 1e-7 r_n).
+    a.rcf = (float)rc;
+    a.shell_inv = skin > 0.0 ? (float)(kShellBins / skin) : 0.0f;
+    a.shell_eps = (float)(1e-4 * rn);
 }
 
 }  // namespace md

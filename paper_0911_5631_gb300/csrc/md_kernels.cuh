@@ -1010,6 +1010,26 @@ __device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int 
     return r2 < a.rn2;
 }
 
+// Shell bin of a list entry at squared distance rr (FP32, as the build
+// computes it): floor((r - r_c) kShellBins / skin), clamped to [0, 7].
+template <class P>
+__device__ __forceinline__ int shell_bin(const Args<P>& a, float rr) {
+    const float r = rr * rsqrtf(fmaxf(rr, 1e-30f));
+    const float t = (r - a.rcf) * a.shell_inv;
+    return t >= 1.0f ? min((int)t, kShellBins - 1) : 0;
+}
+
+// Shell reach of a step: the smallest k in 1..kShellBins with
+// r_c + k skin / kShellBins >= r_c + 2 sqrt(d2max) + margin.  A pair whose
+// distance at the build was beyond that bound is farther than r_c now (each
+// of its atoms has moved at most sqrt(d2max)), so only the entries below the
+// k-th shell boundary need to be read.
+template <class P>
+__device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
+    const float t = fmaf(2.0f, sqrtf(__uint_as_float(d2bits)), a.shell_eps) * a.shell_inv;
+    return t < (float)(kShellBins - 1) ? max((int)ceilf(t), 1) : kShellBins;
+}
+
 // Neighbour-list build (Sec. 3.4): for the atom in cell-ordered slot s, scan
 // the 27 cells around its cell and record every j != i with r < r_n in its
 // column together with the cell-offset code.  The decision is the exact
@@ -1017,8 +1037,17 @@ __device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int 
 // band around r_n^2, the FP64 test the rest.  The three cells of one
 // (c_y, c_z) row sit at base + c_x * stride in the pencil order, so each row
 // costs one index computation and the six range bounds are read together.
+//
+// The first kBuildStage entries wait in shared memory, each with its
+// squared distance, in one 8-byte word stage[t * stride] private to the
+// thread.  A warp runs the candidate loop's accepting code whenever any of
+// its lanes accepts, so that code is only a predicated store; afterwards the
+// entries are written out ordered by shell bin (a counting sort whose bin
+// counts sit in the bytes of one 64-bit word) and lim receives the number
+// of entries below each bin boundary.  An atom with more entries keeps its
+// order of discovery and a lim of "all entries".
 template <class P>
-__device__ __forceinline__ int build_item(const Args<P>& a, int64_t s) {
+__device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* stage, int stride) {
     Counters* C = a.ctr;
     int m = 0;
     const float4 ci = a.cand[s];
@@ -1059,13 +1088,46 @@ __device__ __forceinline__ int build_item(const Args<P>& a, int64_t s) {
                     bool take = rr < lo2;
                     if (!take && rr < hi2) take = within_rn_fp64(a, i, j, k - 1, dy, dz);
                     take = take && t != self;
-                    if (take && m < cap) col[(size_t)m * 32] = j | code;
+                    if (take && m < kBuildStage) stage[m * stride] = make_int2(j | code, __float_as_int(rr));
+                    if (take && m >= kBuildStage && m < cap) col[(size_t)m * 32] = j | code;
                     m += take ? 1 : 0;
                 }
             }
         }
     }
-    a.nn[i] = m < cap ? m : cap;
+    const int kept = m < cap ? m : cap;
+    a.nn[i] = kept;
+    unsigned long long incl = ~0ull;  // lim byte 255: read all entries
+    if (m <= kBuildStage && m <= cap) {
+        unsigned hlo = 0u, hhi = 0u;  // entries of shell bin b in byte b of (hhi:hlo)
+        for (int t = 0; t < m; t++) {
+            const int b = shell_bin(a, __int_as_float(stage[t * stride].y));
+            stage[t * stride].y = b;
+            const unsigned inc = 1u << (8 * (b & 3));
+            hlo += b < 4 ? inc : 0u;
+            hhi += b < 4 ? 0u : inc;
+        }
+        // byte b of incl: entries of bins 0..b, i.e. those below the
+        // boundary r_c + (b + 1) skin / kShellBins (no byte exceeds kBuildStage)
+        incl = (((unsigned long long)hhi << 32) | hlo) * 0x0101010101010101ull;
+        const unsigned long long first = incl << 8;  // exclusive: first slot of each bin
+        unsigned nlo = (unsigned)first, nhi = (unsigned)(first >> 32);
+        for (int t = 0; t < m; t++) {
+            const int2 e = stage[t * stride];
+            const int b = e.y;
+            const int sh = 8 * (b & 3);
+            const int dst = (int)(((b < 4 ? nlo : nhi) >> sh) & 0xffu);
+            const unsigned inc = 1u << sh;
+            nlo += b < 4 ? inc : 0u;
+            nhi += b < 4 ? 0u : inc;
+            col[(size_t)dst * 32] = e.x;
+        }
+    } else {
+        const int ns = min(kept, kBuildStage);
+        for (int t = 0; t < ns; t++) col[(size_t)t * 32] = stage[t * stride].x;
+    }
+#pragma unroll
+    for (int k = 1; k < kShellBins; k++) a.lim[(size_t)(k - 1) * a.n + i] = (unsigned char)(incl >> (8 * (k - 1)));
     if (m > cap) {
         atomicOr(&C->error, kErrOverflow);
         atomicMax(&C->need_cap, m);
@@ -1077,10 +1139,11 @@ template <class P>
 __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
     __shared__ int shm[kBlock / 32];
     __shared__ double shs[kBlock / 32];
+    __shared__ int2 s_stage[kBuildStage * kBlock];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     const int64_t s = gtid();
-    const int m = s < a.n ? build_item<P>(a, s) : 0;
+    const int m = s < a.n ? build_item<P>(a, s, s_stage + threadIdx.x, kBlock) : 0;
     int bm = block_max_int(m, shm);
     double bs = block_sum((double)m, shs);
     if (threadIdx.x == 0) {
@@ -1089,12 +1152,18 @@ __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
     }
 }
 
-// Closes a rebuild: counters, reorder bookkeeping, flag cleared.
+// Closes a rebuild: counters, reorder bookkeeping, flag cleared, and the
+// running maximum of the displacement restarted.  One warp.
 template <class P>
 __global__ void k_rebuild_done(Args<P> a, int guard) {
     Counters* C = a.ctr;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (guard && !C->rebuild_flag) return;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const bool run = !guard || C->rebuild_flag;
+    __syncwarp();  // every lane has read the flag before lane 0 clears it
+    if (!run) return;
+    if (a.d2b)
+        for (int b = threadIdx.x; b < kD2Buckets; b += 32) a.d2b[b * 32] = 0u;
+    if (threadIdx.x != 0) return;
     C->rebuilds += 1;
     if (C->reorder_now) {
         C->reorders += 1;
@@ -1102,6 +1171,8 @@ __global__ void k_rebuild_done(Args<P> a, int guard) {
         C->reorder_now = 0;
     }
     C->rebuild_flag = 0;
+    C->d2max = 0u;  // displacements now count from the new build
+    C->reach = shell_reach(a, 0u);
 }
 
 // Graph prologue: copies the device rebuild flag into the first
@@ -1130,9 +1201,47 @@ __device__ __forceinline__ int decide_rebuild(Counters* C, int cell_list_only, i
 __device__ __forceinline__ float kick(const Args<Mixed>& a, float v, float f) { return fmaf(a.hf, f, v); }
 __device__ __forceinline__ double kick(const Args<F64>& a, double v, double f) { return fma(a.h, f, v); }
 
-// One atom of k_kickdrift; returns whether it has moved skin/2.
+// This block's word of the running maximum of the squared displacement.
 template <class P>
-__device__ __forceinline__ bool kickdrift_item(const Args<P>& a, int64_t i, typename P::pos4* pc) {
+__device__ __forceinline__ unsigned* d2_word(const Args<P>& a) {
+    return a.d2b ? a.d2b + (blockIdx.x % kD2Buckets) * 32 : &a.ctr->d2max;
+}
+
+// The running maximum over all words (warp-wide: every lane of the warp
+// must call it and gets the result).  Reads past L1.
+template <class P>
+__device__ __forceinline__ unsigned d2_gather_warp(const Args<P>& a) {
+    unsigned v = 0u;
+    if (a.d2b) {
+        for (int b = threadIdx.x & 31; b < kD2Buckets; b += 32) v = max(v, __ldcg(a.d2b + b * 32));
+    } else {
+        v = __ldcg(&a.ctr->d2max);
+    }
+    return __reduce_max_sync(0xffffffffu, v);
+}
+
+// Bits of a squared displacement as FP32 (>= 0, so the unsigned order of
+// the bits is the order of the values).
+__device__ __forceinline__ unsigned d2_bits(float d2) { return __float_as_uint(d2); }
+__device__ __forceinline__ unsigned d2_bits(double d2) { return __float_as_uint(cvt::f32(d2)); }
+
+// Largest value over the warp, merged by lane 0 into the running maximum
+// *dst.  The atomic is skipped when a value *dst already held is not
+// smaller: *dst only grows while a kernel runs (it is cleared in another
+// kernel), so the read may come from L1 and be stale, and the atomics,
+// which all go to one address, stay few.  kL2: read past L1 (a persistent
+// kernel whose team clears *dst between steps).  Every lane of the warp
+// must call it.
+template <bool kL2 = false>
+__device__ __forceinline__ void warp_max_into(unsigned v, unsigned* dst) {
+    v = __reduce_max_sync(0xffffffffu, v);
+    if ((threadIdx.x & 31) == 0 && v > (kL2 ? __ldcg(dst) : *dst)) atomicMax(dst, v);
+}
+
+// One atom of k_kickdrift; returns whether it has moved skin/2 and sets
+// d2b to the bits of its squared displacement.
+template <class P>
+__device__ __forceinline__ bool kickdrift_item(const Args<P>& a, int64_t i, typename P::pos4* pc, unsigned& d2b) {
     using real = typename P::real;
     using vel = typename P::vel;
     vel vx = kick(a, a.vx[i], a.fx[i]);
@@ -1146,6 +1255,7 @@ __device__ __forceinline__ bool kickdrift_item(const Args<P>& a, int64_t i, type
     a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
     a.ox[i] = ox; a.oy[i] = oy; a.oz[i] = oz;
     pc[i] = make_pos4(px, py, pz, 0);
+    d2b = d2_bits(d2);
     if constexpr (P::kFp64) return d2 >= a.thr2;
     else return d2 >= a.thr2f;
 }
@@ -1163,25 +1273,40 @@ __global__ void __launch_bounds__(kBlock) k_kickdrift(Args<P> a, long long nstep
     const int par = vw.par;
     int64_t i = gtid();
     bool far = false;
-    if (!err && i < a.n) far = kickdrift_item<P>(a, i, par ? a.pB : a.pA);
+    unsigned d2b = 0u;
+    if (!err && i < a.n) far = kickdrift_item<P>(a, i, par ? a.pB : a.pA, d2b);
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
+    warp_max_into(d2b, d2_word(a));
     if (last_block_done(C)) {
+        const unsigned d2 = threadIdx.x < 32 ? d2_gather_warp(a) : 0u;
         if (threadIdx.x == 0) {
             if (!err) {
                 C->steps_left = nsteps;
                 decide_rebuild(C, a.cell_list_only, a.reorder_interval);
+                C->d2max = d2;
+                C->reach = shell_reach(a, d2);
             }
             C->ticket = 0;
         }
     }
 }
 
+// Entries of atom i < n to read at shell reach k (all of them outside
+// 1..kShellBins-1, where no plane applies).
+template <class P>
+__device__ __forceinline__ int list_count(const Args<P>& a, int64_t i, int k) {
+    int c = 0xff;
+    if (k >= 1 && k < kShellBins) c = a.lim[(size_t)(k - 1) * a.n + i];
+    return c != 0xff ? c : a.nn[i];
+}
+
 // Stages the first rows of the warp's neighbour column block in shared
 // memory (rows below the capacity always exist; unused ones are ignored)
-// and reads atom i's neighbour count.  Every lane of the warp must call it.
+// and reads the number of entries of atom i that the step's shell reach
+// (from the counters) leaves to read.  Every lane of the warp must call it.
 template <class P, bool kCells>
-__device__ __forceinline__ void stage_rows(const Args<P>& a, int64_t i, int* rows, int& cnt, int& staged,
-                                           const int*& col) {
+__device__ __forceinline__ void stage_rows(const Args<P>& a, int64_t i, int reach, int* rows, int& cnt,
+                                           int& staged, const int*& col) {
     cnt = 0;
     staged = 0;
     col = nullptr;
@@ -1192,7 +1317,7 @@ __device__ __forceinline__ void stage_rows(const Args<P>& a, int64_t i, int* row
             for (int c = threadIdx.x & 31; c < staged * 8; c += 32) cp_async16(rows + 4 * c, blk + 4 * c);
         }
         if (i < a.n) {
-            cnt = a.nn[i];
+            cnt = list_count(a, i, reach);
             col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
         }
     }
@@ -1215,7 +1340,8 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
                                           int cnt, const int* col, const int* rows, int staged,
                                           const typename P::pos4* __restrict__ pc, typename P::pos4* pn,
                                           const typename P::pos4* s_shift, typename Queue<P>::item* s_queue,
-                                          bool& far, bool& close, double& ke, double& pe, double& vir) {
+                                          bool& far, bool& close, double& ke, double& pe, double& vir,
+                                          unsigned& d2b) {
     using real = typename P::real;
     using vel = typename P::vel;
     using pos4 = typename P::pos4;
@@ -1266,6 +1392,7 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
             a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
             a.ox[i] = ox; a.oy[i] = oy; a.oz[i] = oz;
             pn[i] = make_pos4(px, py, pz, 0);
+            d2b = d2_bits(d2);
             if constexpr (P::kFp64) far = d2 >= a.thr2;
             else far = d2 >= a.thr2f;
         }
@@ -1296,16 +1423,16 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
     // Requests that do not depend on the counters go out first, so their
     // latency overlaps the counter read: the first rows of the warp's
     // neighbour column block (copied to shared memory; rows below the
-    // capacity always exist, unused ones are ignored) and the neighbour
-    // count.  The pair coordinate q_i comes from the current pair buffer
-    // (bit-identical to pb + o rounded, which wrote it); pb and o are read
-    // after the force loop, where they are needed.
+    // capacity always exist, unused ones are ignored) and the number of
+    // entries to read.  The pair coordinate q_i comes from the current pair
+    // buffer (bit-identical to pb + o rounded, which wrote it); pb and o are
+    // read after the force loop, where they are needed.
     const int64_t i = gtid();
     const bool in = i < a.n;
     int cnt, staged;
     const int* col;
     int* rows = s_rows + (threadIdx.x >> 5) * (kStageRows * 32);
-    stage_rows<P, kCells>(a, i, rows, cnt, staged, col);
+    stage_rows<P, kCells>(a, i, C->reach, rows, cnt, staged, col);
     stage_wait<kCells>();
     const View vw = load_view(C);  // also orders the table fill before its use
     const int err = vw.err;
@@ -1320,10 +1447,12 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
     pos4* pn = par ? a.pA : a.pB;
     bool far = false, close = false;
     double ke = 0.0, pe = 0.0, vir = 0.0;
+    unsigned d2b = 0u;
     step_atom<P, kCells, kFinal>(a, i, in, active, init, energy, cnt, col, rows, staged, pc, pn, s_shift, s_queue,
-                                 far, close, ke, pe, vir);
+                                 far, close, ke, pe, vir, d2b);
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
     if (__any_sync(0xffffffffu, close) && (threadIdx.x & 31) == 0) atomicOr(&C->close_flag, 1);
+    warp_max_into(d2b, d2_word(a));  // the running maximum of the squared displacement
     if constexpr (kFinal) {
         if (energy && active) {
             double bk = block_sum(ke, shs);
@@ -1337,6 +1466,7 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
         }
     }
     if (last_block_done(C)) {
+        const unsigned d2 = threadIdx.x < 32 ? d2_gather_warp(a) : 0u;
         if (threadIdx.x == 0) {
             int need = 0;
             if (misplaced && err == 0) C->error |= kErrInternal;
@@ -1358,10 +1488,25 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
                 C->error |= kErrClose;
                 C->close_flag = 0;
             }
+            C->d2max = d2;
+            C->reach = shell_reach(a, d2);
             if (has_next) cudaGraphSetConditional(next, need ? 1u : 0u);
             C->ticket = 0;
         }
     }
+}
+
+// Profiling aid, not part of a step: adds to ctr->list_reads the number of
+// list entries the next step will read (list_count at the current shell
+// reach, summed over the atoms).
+template <class P>
+__global__ void __launch_bounds__(kBlock) k_count_reads(Args<P> a) {
+    __shared__ double shs[kBlock / 32];
+    const int64_t i = gtid();
+    int c = 0;
+    if (i < a.n && !a.cell_list_only) c = list_count(a, i, a.ctr->reach);
+    const double s = block_sum((double)c, shs);
+    if (threadIdx.x == 0) atomicAdd((unsigned long long*)&a.ctr->list_reads, (unsigned long long)s);
 }
 
 // Step (f) of Sec. 3.1: v <- s v (the product in FP64, stored in the
@@ -1600,9 +1745,10 @@ __device__ __noinline__ void ens_scan(const Args<P>& a, EnsShared& sh) {
 }
 
 // The rebuild branch of one replica (the kernels k_bin .. k_rebuild_done,
-// with team barriers between the phases).
+// with team barriers between the phases).  stage: the block's dynamic
+// shared memory, kBuildStage 8-byte words per thread for the build.
 template <class P>
-__device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh, Team tm) {
+__device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh, int* stage, Team tm) {
     Counters* C = a.ctr;
     const int64_t n = a.n, t0 = tm.first(), dt = tm.stride();
     for (int64_t i = t0; i < n; i += dt) bin_item<P>(a, i);
@@ -1623,7 +1769,7 @@ __device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh, Team t
     int mx = 0;
     long long sum = 0;
     for (int64_t s = t0; s < n; s += dt) {
-        const int m = build_item<P>(a, s);
+        const int m = build_item<P>(a, s, reinterpret_cast<int2*>(stage) + threadIdx.x, (int)blockDim.x);
         mx = max(mx, m);
         sum += m;
     }
@@ -1644,6 +1790,7 @@ __device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh, Team t
             C->reorder_now = 0;
         }
         C->rebuild_flag = 0;
+        C->d2max = 0u;
     }
     tm.sync();
 }
@@ -1663,21 +1810,26 @@ __device__ __noinline__ void ens_step(const Args<P>& a, int* rows, bool init, Te
     const bool energy = init || last;
     const typename P::pos4* pc = par ? a.pB : a.pA;
     typename P::pos4* pn = par ? a.pA : a.pB;
+    // read past L1: other blocks of the team raised it in the last step
+    const int reach = shell_reach(a, __ldcg(&C->d2max));
     bool far = false, close = false;
+    unsigned d2m = 0u;
     const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int64_t nchunks = (a.n + 31) / 32;
     for (int64_t ch = (int64_t)tm.rank * nw + (threadIdx.x >> 5); ch < nchunks; ch += (int64_t)tm.size * nw) {
         const int64_t i = ch * 32 + lane;
         int cnt, staged;
         const int* col;
-        stage_rows<P, false>(a, i, rows, cnt, staged, col);
+        stage_rows<P, false>(a, i, reach, rows, cnt, staged, col);
         stage_wait<false>();
         bool f = false, cl = false;
         double k = 0.0, u = 0.0, w = 0.0;
+        unsigned d2b = 0u;
         step_atom<P, false, kFinal>(a, i, i < a.n, active, init, energy, cnt, col, rows, staged, pc, pn, nullptr,
-                                    nullptr, f, cl, k, u, w);
+                                    nullptr, f, cl, k, u, w, d2b);
         far |= f;
         close |= cl;
+        d2m = max(d2m, d2b);
         if (kFinal && energy) {  // fixed-shape sum over the chunk's 32 atoms
             for (int o = 16; o > 0; o >>= 1) {
                 k += __shfl_xor_sync(0xffffffffu, k, o);
@@ -1694,6 +1846,7 @@ __device__ __noinline__ void ens_step(const Args<P>& a, int* rows, bool init, Te
     }
     if (__any_sync(0xffffffffu, far) && lane == 0) atomicOr(&C->far_flag, 1u);
     if (__any_sync(0xffffffffu, close) && lane == 0) atomicOr(&C->close_flag, 1);
+    warp_max_into<true>(d2m, &C->d2max);
     tm.sync();
     if (kFinal && energy) {
         // chunk sums -> sums of 32 consecutive chunks (fixed shape, in any
@@ -1757,9 +1910,10 @@ __device__ __noinline__ void ens_step(const Args<P>& a, int* rows, bool init, Te
 // One job: load the replica's state when asked (md_set_state), then
 // `nsteps` steps (md_step).  Every block of the team runs it.
 template <class P>
-__device__ __noinline__ void ens_job(const Args<P>& a, EnsShared& sh, int* rows, int init, long long nsteps,
+__device__ __noinline__ void ens_job(const Args<P>& a, EnsShared& sh, int* smem, int init, long long nsteps,
                                      Team tm) {
     Counters* C = a.ctr;
+    int* rows = smem + (threadIdx.x >> 5) * (kStageRows * 32);
     if (init) {
         if (tm.leader()) {
             Counters z = {};
@@ -1770,14 +1924,20 @@ __device__ __noinline__ void ens_job(const Args<P>& a, EnsShared& sh, int* rows,
         tm.sync();
         for (int64_t i = tm.first(); i < a.n; i += tm.stride()) set_state_item<P>(a, i);
         tm.sync();
-        if (C->error == 0) ens_rebuild<P>(a, sh, tm);
+        if (C->error == 0) ens_rebuild<P>(a, sh, smem, tm);
         if (C->error == 0) ens_step<P, true>(a, rows, true, tm);
     }
     if (nsteps > 0 && C->error == 0) {
         bool far = false;
+        unsigned d2m = 0u;
         const int par = C->parity;
-        for (int64_t i = tm.first(); i < a.n; i += tm.stride()) far |= kickdrift_item<P>(a, i, par ? a.pB : a.pA);
+        for (int64_t i = tm.first(); i < a.n; i += tm.stride()) {
+            unsigned d2b = 0u;
+            far |= kickdrift_item<P>(a, i, par ? a.pB : a.pA, d2b);
+            d2m = max(d2m, d2b);
+        }
         if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
+        warp_max_into<true>(d2m, &C->d2max);
         tm.sync();
         if (tm.leader()) {
             C->steps_left = nsteps;
@@ -1785,7 +1945,7 @@ __device__ __noinline__ void ens_job(const Args<P>& a, EnsShared& sh, int* rows,
         }
         tm.sync();
         for (long long st = 0; st < nsteps; st++) {
-            if (C->rebuild_flag) ens_rebuild<P>(a, sh, tm);
+            if (C->rebuild_flag) ens_rebuild<P>(a, sh, smem, tm);
             if (C->error) break;
             if (st + 1 < nsteps) ens_step<P, false>(a, rows, false, tm);
             else ens_step<P, true>(a, rows, false, tm);
@@ -1807,14 +1967,14 @@ __device__ __forceinline__ void ens_load_args(Args<P>& dst, const Args<P>* src) 
 // by whole clusters (when the launch has clusters of more than one block),
 // taken from queue[0] by each cluster's first block; the remaining jobs are
 // run by single blocks, taken from queue[1].  Both lists are in decreasing
-// order of work.  Dynamic shared memory: kStageRows x 32 ints per warp.
+// order of work.  Dynamic shared memory: kEnsSmemInts ints per thread (the
+// step's staged rows, kStageRows x 32 per warp, or the build's staging).
 template <class P>
 __global__ void __launch_bounds__(1024, 1) k_ensemble(const Args<P>* __restrict__ reps, EnsJob* jobs, int njobs,
                                                        int nteam, int* queue) {
-    extern __shared__ __align__(16) int ens_rows[];
+    extern __shared__ __align__(16) int ens_smem[];
     __shared__ EnsShared sh;
     __shared__ __align__(16) Args<P> a;
-    int* rows = ens_rows + (threadIdx.x >> 5) * (kStageRows * 32);
     const unsigned cs = cluster_size();
     if (cs > 1) {
         const Team tm{(int)cluster_rank(), (int)cs};
@@ -1827,7 +1987,7 @@ __global__ void __launch_bounds__(1024, 1) k_ensemble(const Args<P>* __restrict_
             ens_load_args<P>(a, reps + jobs[j].rep);
             if (tm.leader()) jobs[j].t_start = globaltimer_ns();
             tm.sync();
-            ens_job<P>(a, sh, rows, jobs[j].init, jobs[j].nsteps, tm);
+            ens_job<P>(a, sh, ens_smem, jobs[j].init, jobs[j].nsteps, tm);
             if (tm.leader()) jobs[j].t_end = globaltimer_ns();
         }
     }
@@ -1840,7 +2000,7 @@ __global__ void __launch_bounds__(1024, 1) k_ensemble(const Args<P>* __restrict_
         ens_load_args<P>(a, reps + jobs[j].rep);
         if (threadIdx.x == 0) jobs[j].t_start = globaltimer_ns();
         __syncthreads();
-        ens_job<P>(a, sh, rows, jobs[j].init, jobs[j].nsteps, solo);
+        ens_job<P>(a, sh, ens_smem, jobs[j].init, jobs[j].nsteps, solo);
         if (threadIdx.x == 0) jobs[j].t_end = globaltimer_ns();
         __syncthreads();
     }
@@ -1881,6 +2041,7 @@ KernelTable<P> make_kernel_table() {
     t.clear_overflow = (void*)k_clear_overflow<P>;
     t.selftest = (void*)k_selftest<P>;
     t.rescale = (void*)k_rescale<P>;
+    t.count_reads = (void*)k_count_reads<P>;
     if constexpr (!P::kFp64) t.ensemble = (void*)k_ensemble<P>;
     else t.ensemble = nullptr;
     return t;

@@ -32,6 +32,7 @@ struct KernelTable {
     void* clear_overflow;
     void* selftest;
     void* rescale;
+    void* count_reads;
     void* ensemble;  // mixed form only (nullptr for FP64)
 };
 

@@ -152,6 +152,37 @@ def test_trajectory_segment(case, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", [(2916, 0.8, 1.5, 0.8, (1, 1, 1), 11), (3000, 0.95, 1.2, 0.6, (1, 1, 1), 12)],
+                         ids=["skin0.8", "rho0.95_skin0.6"])
+def test_trajectory_across_shell_bins(case, prec):
+    # A step reads only the entries whose distance at the build lies within
+    # r_c + 2 (largest displacement so far): a wide skin spreads the list
+    # over shell bins of width 0.1; at rho 0.95 with skin 0.6 the lists hold
+    # about 21 entries, so atoms with sorted lists and atoms with lists too
+    # long to sort (read whole) sit side by side.  Long segments cross
+    # several rebuilds.
+    n, rho, T, skin, aspect, seed = case
+    pos, vel, L = state(n, rho, T, seed, aspect=aspect)
+    out = oracle.run(oracle.wrap(pos, L), vel, L, RC, skin, DT, 300, record=False)
+    pos, vel = out["pos"], out["vel"]
+    k = 60
+    s = sim(pos, vel, L, skin=skin, precision=prec)
+    ref = oracle.run(pos, vel, L, RC, skin, DT, k)
+    pairs, entries = s.neighbor_pairs()
+    s.step(k)
+    p, v = s.get_state()
+    f_rms = float(np.sqrt(np.mean(ref["f"] ** 2)))
+    dv, dx = _trajectory_tol(prec, f_rms, k)
+    assert np.sqrt(np.mean((v - ref["vel"]) ** 2)) <= dv
+    assert np.sqrt(np.mean(min_image(p - ref["pos"], L) ** 2)) <= dx
+    m = s.measure()
+    assert m["rebuilds"] >= 2
+    if rho > 0.9:
+        assert m["max_neighbors"] > 21 and entries / n < 24  # both kinds of list
+    s.close()
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_cell_list_only_segments(prec):
     # soft-sphere fluid of 2048 atoms (FCC 8^3 x 4) at rho 0.8, T 1, forces
     # straight from the cells every step; compared in 100-step segments, the
