@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--ens-steps", type=int, default=inputs.ENSEMBLE["steps"])
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace lines")
     ap.add_argument("--no-lj", action="store_true", help="skip the Lennard-Jones line")
-    ap.add_argument("--ablations", action="store_true", help="add the reorder-interval ablation")
+    ap.add_argument("--ablations", action="store_true", help="add the reorder-interval and shell-bin ablations")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-low-rate", type=float, default=10.0,
                     help="arrival rate of the second, below-saturation trace")
@@ -325,12 +325,14 @@ def lj_bench(md, torch, stream, device, steps, chunk=100):
 
 def ablations(md, torch, stream, device, pos, vel, L, cfg, chunk=100, steps=5):
     """The paper's ablations on the 1M workload (mixed form): the reorder
-    interval (Tables 7, 8; 0 = never after the load) -- atom-steps/s and the
-    step kernel's time, each from an equilibrated state."""
+    interval (Tables 7, 8; 0 = never after the load), and lists read whole at
+    every step as in the paper (shell bins off) -- atom-steps/s, the step
+    kernel's time and the rebuild branch's time, each from an equilibrated
+    state."""
     out = []
-    for interval in (0, 20, 100, 500):
+    for interval, bins in ((0, True), (20, True), (100, True), (500, True), (100, False)):
         s = md.Simulation(L, cfg["n"], RC, cfg["skin"], DT, precision="mixed", reorder_interval=interval,
-                          stream=stream.cuda_stream, device=device)
+                          stream=stream.cuda_stream, device=device, shell_bins=bins)
         try:
             s.set_state(pos, vel)
             s.step(1000)  # long enough for the storage order to drift from the cell order
@@ -349,8 +351,11 @@ def ablations(md, torch, stream, device, pos, vel, L, cfg, chunk=100, steps=5):
             k1 = s.kernel_stats()
             s.set_profiling(False)
             kl = k1["step_kernel_launches"] - k0["step_kernel_launches"]
-            out.append({"reorder_interval": interval, "value": cfg["n"] * chunk * steps / (ms / 1e3), "unit": UNIT,
+            rb = k1["rebuilds_timed"] - k0["rebuilds_timed"]
+            out.append({"reorder_interval": interval, "shell_bins": bins,
+                        "value": cfg["n"] * chunk * steps / (ms / 1e3), "unit": UNIT,
                         "step_kernel_us": 1e3 * (k1["step_kernel_ms"] - k0["step_kernel_ms"]) / max(kl, 1),
+                        "rebuild_us": 1e3 * (k1["rebuild_ms"] - k0["rebuild_ms"]) / rb if rb else None,
                         "reorders": s.measure()["reorders"]})
         finally:
             s.close()

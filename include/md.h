@@ -82,7 +82,12 @@ typedef struct md_params {
                                  node; 0: plain stream launches (same results,
                                  bit for bit).                                 */
     int32_t device;           /* CUDA device ordinal; -1 (default) = current   */
-    int32_t reserved0;
+    int32_t shell_bins;       /* 1 (default): the build sorts each atom's list
+                                 by distance, and a step reads only the entries
+                                 that the largest displacement since the build
+                                 can have brought inside r_c.  0: every step
+                                 reads every entry (the same forces; in the
+                                 mixed form the same bits).                    */
     double ushift;            /* constant added to Eq. (1) for r < r_c.  NaN
                                  (default) = automatic: +1 (epsilon) when r_c is
                                  2^(1/6) to 1e-12 relative (the soft-sphere

@@ -57,7 +57,7 @@ class md_params(C.Structure):
         ("nbr_capacity", C.c_int32),
         ("use_graphs", C.c_int32),
         ("device", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("shell_bins", C.c_int32),
         ("ushift", C.c_double),
         ("stream", C.c_void_p),
         ("reserved", C.c_int64 * 6),
@@ -368,8 +368,9 @@ class Simulation:
 
     def __init__(self, box, n, rc=WCA_RC, skin=0.4, dt=0.005, precision="mixed", reorder_interval=100,
                  cell_list_only=False, even_cells=False, nbr_capacity=0, use_graphs=True, ushift=None,
-                 stream=None, device=-1):
+                 stream=None, device=-1, shell_bins=True):
         p = md_default_params()
+        p.shell_bins = int(bool(shell_bins))
         p.precision = MD_PREC_FP64 if precision in ("fp64", MD_PREC_FP64) else MD_PREC_MIXED
         p.reorder_interval = int(reorder_interval)
         p.cell_list_only = int(bool(cell_list_only))

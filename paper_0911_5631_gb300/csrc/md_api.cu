@@ -170,7 +170,7 @@ struct Sim : SimBase {
     }
 
     void fill_scalars(int64_t n) {
-        fill_args_scalars(a, plan, box, n, rc, skin, dt, prm.cell_list_only, prm.reorder_interval);
+        fill_args_scalars(a, plan, box, n, rc, skin, dt, prm.cell_list_only, prm.reorder_interval, prm.shell_bins);
     }
 
     int allocate() {
@@ -778,6 +778,7 @@ void md_default_params(md_params* p) {
     p->nbr_capacity = 0;
     p->use_graphs = 1;
     p->device = -1;
+    p->shell_bins = 1;
     p->ushift = NAN;
     p->stream = nullptr;
 }

@@ -122,6 +122,8 @@ struct alignas(16) Args {
     int nblocks;        // ceil(n / kBlock)
     int cell_list_only;
     int reorder_interval;
+    int shell_bins;     // lists sorted by shell bin, steps read up to the shell reach
+    int pad0;
 
     double L[3], hL[3], invL[3], invW[3];
     double w[3];        // cell widths

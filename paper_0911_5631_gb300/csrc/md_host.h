@@ -89,7 +89,7 @@ inline int resolve_plan(const double box[3], int64_t n, double rc, double skin, 
 // Scalar members of Args from a plan.
 template <class P>
 void fill_args_scalars(Args<P>& a, const md_plan_t& plan, const double box[3], int64_t n, double rc, double skin,
-                       double dt, int cell_list_only, int reorder_interval) {
+                       double dt, int cell_list_only, int reorder_interval, int shell_bins = 1) {
     a.n = n;
     a.cap = plan.nbr_capacity;
     a.ncells = (int)plan.n_cells;
@@ -108,6 +108,7 @@ void fill_args_scalars(Args<P>& a, const md_plan_t& plan, const double box[3], i
     a.nblocks = (int)((n + kBlock - 1) / kBlock);
     a.cell_list_only = cell_list_only;
     a.reorder_interval = reorder_interval;
+    a.shell_bins = shell_bins != 0;
     a.dt = dt;
     a.h = 0.5 * dt;
     a.dtf = (float)dt;

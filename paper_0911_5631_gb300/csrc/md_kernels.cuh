@@ -1026,6 +1026,7 @@ __device__ __forceinline__ int shell_bin(const Args<P>& a, float rr) {
 // k-th shell boundary need to be read.
 template <class P>
 __device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
+    if (!a.shell_bins) return kShellBins;
     const float t = fmaf(2.0f, sqrtf(__uint_as_float(d2bits)), a.shell_eps) * a.shell_inv;
     return t < (float)(kShellBins - 1) ? max((int)ceilf(t), 1) : kShellBins;
 }
@@ -1046,8 +1047,8 @@ __device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
 // counts sit in the bytes of one 64-bit word) and lim receives the number
 // of entries below each bin boundary.  An atom with more entries keeps its
 // order of discovery and a lim of "all entries".
-template <class P>
-__device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* stage, int stride) {
+template <class P, bool kSort>
+__device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* stage, int stride) {
     Counters* C = a.ctr;
     int m = 0;
     const float4 ci = a.cand[s];
@@ -1088,8 +1089,12 @@ __device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* sta
                     bool take = rr < lo2;
                     if (!take && rr < hi2) take = within_rn_fp64(a, i, j, k - 1, dy, dz);
                     take = take && t != self;
-                    if (take && m < kBuildStage) stage[m * stride] = make_int2(j | code, __float_as_int(rr));
-                    if (take && m >= kBuildStage && m < cap) col[(size_t)m * 32] = j | code;
+                    if constexpr (kSort) {
+                        if (take && m < kBuildStage) stage[m * stride] = make_int2(j | code, __float_as_int(rr));
+                        if (take && m >= kBuildStage && m < cap) col[(size_t)m * 32] = j | code;
+                    } else {
+                        if (take && m < cap) col[(size_t)m * 32] = j | code;
+                    }
                     m += take ? 1 : 0;
                 }
             }
@@ -1098,7 +1103,7 @@ __device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* sta
     const int kept = m < cap ? m : cap;
     a.nn[i] = kept;
     unsigned long long incl = ~0ull;  // lim byte 255: read all entries
-    if (m <= kBuildStage && m <= cap) {
+    if (kSort && m <= kBuildStage && m <= cap) {
         unsigned hlo = 0u, hhi = 0u;  // entries of shell bin b in byte b of (hhi:hlo)
         for (int t = 0; t < m; t++) {
             const int b = shell_bin(a, __int_as_float(stage[t * stride].y));
@@ -1122,17 +1127,25 @@ __device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* sta
             nhi += b < 4 ? 0u : inc;
             col[(size_t)dst * 32] = e.x;
         }
-    } else {
+    } else if (kSort) {
         const int ns = min(kept, kBuildStage);
         for (int t = 0; t < ns; t++) col[(size_t)t * 32] = stage[t * stride].x;
     }
+    if constexpr (kSort) {
 #pragma unroll
-    for (int k = 1; k < kShellBins; k++) a.lim[(size_t)(k - 1) * a.n + i] = (unsigned char)(incl >> (8 * (k - 1)));
+        for (int k = 1; k < kShellBins; k++)
+            a.lim[(size_t)(k - 1) * a.n + i] = (unsigned char)(incl >> (8 * (k - 1)));
+    }
     if (m > cap) {
         atomicOr(&C->error, kErrOverflow);
         atomicMax(&C->need_cap, m);
     }
     return m;
+}
+
+template <class P>
+__device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* stage, int stride) {
+    return a.shell_bins ? build_item_t<P, true>(a, s, stage, stride) : build_item_t<P, false>(a, s, stage, stride);
 }
 
 template <class P>

@@ -183,6 +183,30 @@ def test_trajectory_across_shell_bins(case, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_shell_bins_change_no_force(prec):
+    # A step that reads only the entries within r_c + 2 (largest displacement)
+    # of their build distance computes the forces of reading every entry.
+    # The mixed form sums in integers, so the trajectories agree bit for bit;
+    # the FP64 form sums in list order, which the sorting changes.
+    pos, vel, L, skin = _fluid(CASES[0])
+    k = 200 if prec == "mixed" else 40
+    runs = []
+    for bins in (True, False):
+        s = sim(pos, vel, L, skin=skin, precision=prec, shell_bins=bins)
+        s.step(k)
+        p, v = s.get_state()
+        runs.append((p, v, s.measure()))
+        s.close()
+    (p1, v1, m1), (p0, v0, m0) = runs
+    assert m1["rebuilds"] == m0["rebuilds"] >= 4
+    if prec == "mixed":
+        assert np.array_equal(p1, p0) and np.array_equal(v1, v0)
+    else:
+        assert np.abs(v1 - v0).max() < 1e-10
+        assert np.abs(min_image(p1 - p0, L)).max() < 1e-11
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_cell_list_only_segments(prec):
     # soft-sphere fluid of 2048 atoms (FCC 8^3 x 4) at rho 0.8, T 1, forces
     # straight from the cells every step; compared in 100-step segments, the
