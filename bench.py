@@ -184,10 +184,10 @@ def run_reference(args):
     pos = oracle.wrap(pos, L)
     sample = 4  # MD steps per benchmark step, from the lattice start
     for _ in range(args.warmup):
-        oracle.run(pos, vel, L, RC, cfg["skin"], DT, sample, record=False)
+        oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, sample, record=False)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.run(pos, vel, L, RC, cfg["skin"], DT, sample, record=False)
+        oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, sample, record=False)
     t = time.perf_counter() - t0
     value = n * sample * args.steps / t
     line = {
@@ -211,11 +211,11 @@ def cpu_baseline(pos, vel, L, cfg, seconds=15.0):
     n = pos.shape[0]
     p = oracle.wrap(pos, L)
     t0 = time.perf_counter()
-    oracle.run(p, vel, L, RC, cfg["skin"], DT, 2, record=False)
+    oracle.run(p, vel, L, cfg.get("rc", RC), cfg["skin"], DT, 2, record=False)
     t1 = time.perf_counter() - t0
     steps = int(max(4, min(400, seconds / max(t1 / 2, 1e-3))))
     t0 = time.perf_counter()
-    oracle.run(p, vel, L, RC, cfg["skin"], DT, steps, record=False)
+    oracle.run(p, vel, L, cfg.get("rc", RC), cfg["skin"], DT, steps, record=False)
     t = time.perf_counter() - t0
     return {"value": n * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d MD steps of the %d-atom equilibrated state (includes the initial list build), "
@@ -331,7 +331,7 @@ def ablations(md, torch, stream, device, pos, vel, L, cfg, chunk=100, steps=5):
     state."""
     out = []
     for interval, bins in ((0, True), (20, True), (100, True), (500, True), (100, False)):
-        s = md.Simulation(L, cfg["n"], RC, cfg["skin"], DT, precision="mixed", reorder_interval=interval,
+        s = md.Simulation(L, cfg["n"], cfg.get("rc", RC), cfg["skin"], DT, precision="mixed", reorder_interval=interval,
                           stream=stream.cuda_stream, device=device, shell_bins=bins)
         try:
             s.set_state(pos, vel)
@@ -378,7 +378,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
 
     def make(precision):
-        s = md.Simulation(L, n, RC, cfg["skin"], DT, precision=precision, reorder_interval=100,
+        s = md.Simulation(L, n, cfg.get("rc", RC), cfg["skin"], DT, precision=precision, reorder_interval=100,
                           use_graphs=not args.eager, stream=stream.cuda_stream, device=local)
         s.set_state(pos, vel)
         return s
