@@ -1479,27 +1479,42 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
         }
     }
     if (last_block_done(C)) {
+        // The counters this block reads go out together (one round trip to
+        // L2 on the step's serial tail); every other block has finished.
+        int err0 = 0, close0 = 0;
+        unsigned far0 = 0u;
+        long long step0 = 0, since0 = 0;
+        if (threadIdx.x == 0) {
+            err0 = C->error;
+            close0 = C->close_flag;
+            far0 = C->far_flag;
+            step0 = C->step;
+            since0 = C->since_reorder;
+        }
         const unsigned d2 = threadIdx.x < 32 ? d2_gather_warp(a) : 0u;
         if (threadIdx.x == 0) {
             int need = 0;
-            if (misplaced && err == 0) C->error |= kErrInternal;
+            int errn = err0;
+            if (misplaced && err == 0) errn |= kErrInternal;
+            if (close0) errn |= kErrClose;
+            if (errn != err0) C->error = errn;
+            if (close0) C->close_flag = 0;
             if (active && !init) {
                 C->steps_left = left - 1;
-                C->step += 1;
-                C->since_reorder += 1;
+                C->step = step0 + 1;
+                C->since_reorder = since0 + 1;
                 if (!last) {
                     C->parity = par ^ 1;
-                    need = decide_rebuild(C, a.cell_list_only, a.reorder_interval);
+                    // the rebuild decision of decide_rebuild, on the values read above
+                    need = (far0 != 0u) || a.cell_list_only;
+                    C->rebuild_flag = need;
+                    C->reorder_now = need && a.reorder_interval > 0 && since0 + 1 >= a.reorder_interval;
                 } else {
-                    C->far_flag = 0u;
                     C->rebuild_flag = 0;
                 }
+                C->far_flag = 0u;
             } else if (!init) {
                 C->far_flag = 0u;
-            }
-            if (C->close_flag) {
-                C->error |= kErrClose;
-                C->close_flag = 0;
             }
             C->d2max = d2;
             C->reach = shell_reach(a, d2);
