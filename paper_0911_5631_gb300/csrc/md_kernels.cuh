@@ -1724,6 +1724,17 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+// Profiling aid: keeps the GPU busy for about ns nanoseconds (at most 2^20
+// clock reads), so that the events queued after it are not timestamped
+// before the host has queued the kernels they bracket.
+template <class P>
+__global__ void k_spin(long long ns) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const unsigned long long t0 = globaltimer_ns();
+    for (int k = 0; k < (1 << 20); k++)
+        if (globaltimer_ns() - t0 >= (unsigned long long)ns) break;
+}
+
 // Exclusive scan of the replica's cell counts into cell_start, by one block,
 // and the largest occupancy (the paper's N_l) into C->max_occ.
 template <class P>
@@ -2070,6 +2081,7 @@ KernelTable<P> make_kernel_table() {
     t.selftest = (void*)k_selftest<P>;
     t.rescale = (void*)k_rescale<P>;
     t.count_reads = (void*)k_count_reads<P>;
+    t.spin = (void*)k_spin<P>;
     if constexpr (!P::kFp64) t.ensemble = (void*)k_ensemble<P>;
     else t.ensemble = nullptr;
     return t;

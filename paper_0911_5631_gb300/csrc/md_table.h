@@ -33,6 +33,7 @@ struct KernelTable {
     void* selftest;
     void* rescale;
     void* count_reads;
+    void* spin;
     void* ensemble;  // mixed form only (nullptr for FP64)
 };
 
