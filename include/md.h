@@ -134,9 +134,10 @@ typedef struct md_kernel_stats_t {
     int64_t step_kernel_launches; /* force+integrate launches timed below       */
     double step_kernel_ms;    /* summed CUDA-event time of those launches       */
     int64_t step_kernel_atoms;/* atoms processed by them                        */
-    int64_t step_kernel_bytes;/* algorithmic bytes moved by them: per atom 120 B
-                                 of state (188 B in FP64), 1 B of list count
-                                 and 4 B per list entry the step reads      */
+    int64_t step_kernel_bytes;/* algorithmic bytes moved by them: per atom 116 B
+                                 of state (184 B in FP64), the list count (1 B
+                                 with shell_bins, else 4 B) and 4 B per list
+                                 entry the step reads                        */
     int64_t rebuilds_timed;   /* rebuild branches (Sec. 3.1 (b)) timed below    */
     double rebuild_ms;        /* their summed CUDA-event time                   */
 } md_kernel_stats_t;

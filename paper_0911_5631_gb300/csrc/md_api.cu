@@ -429,7 +429,12 @@ struct Sim : SimBase {
                 int rr = read_counters(&c);
                 if (rr) return rr;
                 MD_CUDA(cudaMemsetAsync(&a.ctr->list_reads, 0, sizeof(long long), stream));
-                const int64_t base = (P::kFp64 ? 188 : 120) + (prm.cell_list_only ? 0 : 1);
+                // per atom: pb, o, v, the new pair coordinate and the gathered
+                // coordinates (116 B; 184 B in FP64), the list count (a byte
+                // of lim with shell bins, else nn); the cells-only variant
+                // keeps the 120 / 188 B of state and count of the list form
+                const int64_t base = prm.cell_list_only ? (P::kFp64 ? 188 : 120)
+                                                        : (P::kFp64 ? 184 : 116) + (prm.shell_bins ? 1 : 4);
                 step_bytes += nsteps * base * a.n + 4 * c.list_reads;
             }
         }

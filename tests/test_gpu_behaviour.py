@@ -147,3 +147,34 @@ def test_energy_drift(prec):
     drift = abs(e[-100:].mean() - e[100:200].mean())
     assert drift <= 1e-4
     s.close()
+
+
+def test_profiled_bytes_count_the_entries_read():
+    # In profiling mode the algorithmic bytes of the step kernel are 116 B
+    # of per-atom state, the list count (1 B with shell bins, else 4 B) and
+    # 4 B for every list entry the step reads.  Without shell bins a step reads the whole list; with them it
+    # reads fewer entries, but never fewer than the interacting ones.
+    pos, vel, L = state(4000, 0.8, 1.0, 17)
+    out = oracle.run(oracle.wrap(pos, L), vel, L, RC, 0.4, DT, 200, record=False)
+    res = {}
+    for bins in (True, False):
+        s = sim(out["pos"], out["vel"], L, skin=0.4, shell_bins=bins, use_graphs=False)
+        s.set_profiling(True)
+        k0 = s.kernel_stats()
+        s.step(60)
+        k1 = s.kernel_stats()
+        m = s.measure()
+        s.close()
+        launches = k1["step_kernel_launches"] - k0["step_kernel_launches"]
+        base = 116 + (1 if bins else 4)
+        reads = ((k1["step_kernel_bytes"] - k0["step_kernel_bytes"]) - base * 4000 * launches) / 4
+        assert launches == 60 and reads == int(reads)
+        res[bins] = (reads, m)
+    reads_on, m_on = res[True]
+    reads_off, m_off = res[False]
+    assert m_on["rebuilds"] == m_off["rebuilds"]
+    # every entry read: between the smallest and largest list of the run
+    assert reads_off / 60 <= 1.2 * m_off["list_entries"] and reads_off / 60 >= 0.8 * m_off["list_entries"]
+    # the shell bins read fewer, but never fewer than the interacting pairs
+    # (about a third of the list for this state)
+    assert 0.3 * reads_off < reads_on < reads_off
