@@ -119,7 +119,26 @@ def test_ushift_rule(libmd):
 def test_default_params(libmd):
     p = md.md_default_params()
     assert p.precision == md.MD_PREC_MIXED and p.reorder_interval == 100 and p.use_graphs == 1
-    assert np.isnan(p.ushift) and p.device == -1
+    assert np.isnan(p.ushift) and p.device == -1 and p.shell_bins == 1
+
+
+def test_plan_bytes_include_the_shell_bin_counts(libmd):
+    # 7 planes of one byte per atom hold the entry counts below the shell-bin
+    # boundaries; they are part of the device footprint in both forms
+    box = [20.0] * 3
+    for prec in (md.MD_PREC_MIXED, md.MD_PREC_FP64):
+        p = md.md_default_params()
+        p.precision = prec
+        p.nbr_capacity = 48
+        b1 = md.md_plan(box, 4000, md.WCA_RC, 0.4, 0.005, p).device_bytes
+        b2 = md.md_plan(box, 8000, md.WCA_RC, 0.4, 0.005, p).device_bytes
+        per_atom = (b2 - b1) / 4000
+        real = 8 if prec == md.MD_PREC_FP64 else 4
+        pos4 = 32 if prec == md.MD_PREC_FP64 else 16
+        state = 3 * 4 + 3 * real + 24 + 3 * real + 3 * real + 2 * pos4 + 16 + 8 + 3 * real + 24 + 3 * real
+        # order, nn, lim, io, list; the per-block energy partials add 24 B
+        # per 256 atoms
+        assert per_atom == pytest.approx(state + 4 + 4 + 7 + 48 + 48 * 4 + 24 / 256, abs=0.01)
 
 
 def test_ensemble_replica_bytes_needs_no_gpu(libmd):
