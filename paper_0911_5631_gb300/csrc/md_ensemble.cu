@@ -165,7 +165,16 @@ struct md_ensemble {
     int max_replicas = 0;
     EnsJob* d_jobs = nullptr;
     int jobs_cap = 0;
-    int* d_next = nullptr;
+    int* d_next = nullptr;      // {queue[0], queue[1], njobs, nteam} of a launch
+    // Launches are replayed from CUDA graphs, one per launch shape (and job
+    // buffer): each run copies the job list and the header, then launches
+    // the graph.
+    struct Launch {
+        int block = 0, grid = 0, cluster = 0;
+        EnsJob* jobs = nullptr;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::vector<Launch> graphs;
     EnsJob* h_jobs = nullptr;  // pinned copy of the last run's jobs
     int h_jobs_cap = 0;
     int last_njobs = 0;
@@ -256,9 +265,10 @@ int launch_run(md_ensemble* e, const std::vector<EnsJob>& jobs, int nteam, int b
     if (r) return r;
     // from pageable memory: the call has read `jobs` when it returns
     ENS_CUDA(cudaMemcpyAsync(e->d_jobs, jobs.data(), sizeof(EnsJob) * jobs.size(), cudaMemcpyHostToDevice, e->stream));
-    ENS_CUDA(cudaMemsetAsync(e->d_next, 0, 2 * sizeof(int), e->stream));
     int nj = (int)jobs.size();
     if (nteam == 0) cluster = 1;
+    const int hdr[4] = {0, 0, nj, nteam};  // pageable too: read when the call returns
+    ENS_CUDA(cudaMemcpyAsync(e->d_next, hdr, sizeof(hdr), cudaMemcpyHostToDevice, e->stream));
     size_t smem = (size_t)block * kEnsSmemInts * sizeof(int);
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -287,13 +297,33 @@ int launch_run(md_ensemble* e, const std::vector<EnsJob>& jobs, int nteam, int b
             g = std::max(1, per_sm) * sms;
         }
     }
-    // no more blocks than work for them (teams count as `cluster` blocks)
-    const int useful = nteam * cluster + (nj - nteam);
-    g = std::min(g, std::max(useful, cluster));
     if (cluster > 1) g = (g + cluster - 1) / cluster * cluster;
     cfg.gridDim = dim3(g);
-    void* args[] = {(void*)&e->d_args, (void*)&e->d_jobs, (void*)&nj, (void*)&nteam, (void*)&e->d_next};
-    ENS_CUDA(cudaLaunchKernelExC(&cfg, e->kt.ensemble, args));
+    // blocks without a job leave at their first queue read, so one graph
+    // per shape serves every job list
+    md_ensemble::Launch* lg = nullptr;
+    for (auto& x : e->graphs)
+        if (x.block == block && x.grid == g && x.cluster == cluster && x.jobs == e->d_jobs) lg = &x;
+    if (!lg) {
+        void* args[] = {(void*)&e->d_args, (void*)&e->d_jobs, (void*)&e->d_next};
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ENS_CUDA(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t lc = cudaLaunchKernelExC(&cfg, e->kt.ensemble, args);
+        cudaError_t ec = cudaStreamEndCapture(e->stream, &graph);
+        if (lc != cudaSuccess || ec != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            e->err = std::string("capturing the ensemble launch: ") + cudaGetErrorString(lc != cudaSuccess ? lc : ec);
+            return MD_ECUDA;
+        }
+        cudaError_t ic = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        ENS_CUDA(ic);
+        e->graphs.push_back({block, g, cluster, e->d_jobs, exec});
+        lg = &e->graphs.back();
+    }
+    ENS_CUDA(cudaGraphLaunch(lg->exec, e->stream));
     e->last_njobs = nj;
     e->jobs_valid = false;
     e->runs++;
@@ -407,7 +437,7 @@ int md_ensemble_create(int64_t arena_bytes, int32_t max_replicas, int32_t device
     e->arena_bytes = arena_bytes;
     e->alloc.reset(arena_bytes);
     if (cudaMalloc(&e->d_args, sizeof(A) * (size_t)max_replicas) != cudaSuccess ||
-        cudaMalloc(&e->d_next, 2 * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&e->d_next, 4 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         e->err = "cannot allocate the replica table";
         return fail(MD_ENOMEM);
@@ -732,6 +762,8 @@ void md_ensemble_destroy(md_ensemble* e) {
     if (e->d_args) cudaFree(e->d_args);
     if (e->d_jobs) cudaFree(e->d_jobs);
     if (e->d_next) cudaFree(e->d_next);
+    for (auto& x : e->graphs)
+        if (x.exec) cudaGraphExecDestroy(x.exec);
     if (e->h_jobs) cudaFreeHost(e->h_jobs);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
     delete e;

@@ -2002,15 +2002,17 @@ __device__ __forceinline__ void ens_load_args(Args<P>& dst, const Args<P>* src) 
     for (int k = threadIdx.x; k < (int)(sizeof(Args<P>) / 16); k += blockDim.x) d4[k] = s4[k];
 }
 
-// The per-replica engine.  Jobs [0, nteam) -- the big replicas -- are run
-// by whole clusters (when the launch has clusters of more than one block),
-// taken from queue[0] by each cluster's first block; the remaining jobs are
-// run by single blocks, taken from queue[1].  Both lists are in decreasing
-// order of work.  Dynamic shared memory: kEnsSmemInts ints per thread (the
+// The per-replica engine.  hdr = {queue[0], queue[1], njobs, nteam}, written
+// by the host before each launch, so that one captured launch serves every
+// run.  Jobs [0, nteam) -- the big replicas -- are run by whole clusters
+// (when the launch has clusters of more than one block), taken from queue[0]
+// by each cluster's first block; the remaining jobs are run by single blocks,
+// taken from queue[1].  Both lists are in decreasing order of work.  Dynamic shared memory: kEnsSmemInts ints per thread (the
 // step's staged rows, kStageRows x 32 per warp, or the build's staging).
 template <class P>
-__global__ void __launch_bounds__(1024, 1) k_ensemble(const Args<P>* __restrict__ reps, EnsJob* jobs, int njobs,
-                                                       int nteam, int* queue) {
+__global__ void __launch_bounds__(1024, 1) k_ensemble(const Args<P>* __restrict__ reps, EnsJob* jobs, int* hdr) {
+    int* queue = hdr;
+    const int njobs = hdr[2], nteam = hdr[3];
     extern __shared__ __align__(16) int ens_smem[];
     __shared__ EnsShared sh;
     __shared__ __align__(16) Args<P> a;
