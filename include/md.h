@@ -278,7 +278,8 @@ int md_forces_noalloc(const double box[3], int64_t n, double rc, double ushift, 
  * independent replicas of the mixed form (each its own box, N, r_c, skin,
  * dt and state) in one device arena, and md_ensemble_run advances any
  * subset of them in a single kernel launch: each replica is taken by one
- * thread block, which runs Sec. 3.1's steps (a)-(e) for it exactly as
+ * thread block, or by a thread-block cluster when it is large (see
+ * md_ensemble_set_shape), which runs Sec. 3.1's steps (a)-(e) for it as
  * md_set_state/md_step do -- binning, neighbour-list rebuilds at skin/2,
  * reorders every reorder_interval steps, forces, the velocity-Verlet
  * update.  Replicas share nothing, so a replica's trajectory does not
@@ -326,7 +327,10 @@ int md_ensemble_remove(md_ensemble* e, int32_t id);
 
 /* Advances replicas ids[0..count) by nsteps[k] >= 0 steps each in one
  * launch (asynchronous; replicas added since their last run are loaded
- * first, so nsteps 0 only loads them).  An id may appear once per call. */
+ * first, so nsteps 0 only loads them).  An id may appear once per call.
+ * The launch is replayed from a CUDA graph captured on the ensemble's stream
+ * the first time a launch shape is used; a stream that cannot be captured
+ * (the legacy default stream) gives MD_ECUDA. */
 int md_ensemble_run(md_ensemble* e, int32_t count, const int32_t* ids, const int64_t* nsteps);
 
 /* Waits for the ensemble's stream. */
