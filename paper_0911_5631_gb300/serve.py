@@ -78,12 +78,15 @@ class Server:
 
     def __init__(self, budget_bytes: int, slice_steps: int = 200, big_atoms: int = 65536, arena_fraction=0.5,
                  max_replicas: int = 4096, device: int = -1, stream=None, keep_results: bool = True,
-                 slice_atom_steps: int = 2_000_000):
+                 slice_atom_steps: int = 2_000_000, ensemble=None):
         self.arena_bytes = int(budget_bytes * arena_fraction)
         self.solo_budget = int(budget_bytes) - self.arena_bytes
         self.solo_used = 0
         self.device = device
-        self.ens = Ensemble(self.arena_bytes, max_replicas=max_replicas, device=device, stream=stream)
+        # `ensemble`: an engine with the Ensemble interface over an arena of
+        # arena_bytes (the scheduler's own tests pass a host-side stand-in)
+        self.ens = ensemble if ensemble is not None else Ensemble(self.arena_bytes, max_replicas=max_replicas,
+                                                                  device=device, stream=stream)
         # big ensemble members run on clusters of team_blocks 1024-thread blocks
         self.team_atoms, self.team_blocks = 8192, 8
         self.ens.set_shape(1024, 0, self.team_blocks, self.team_atoms)
