@@ -45,10 +45,9 @@ extern "C" {
 #define MD_ECUDA      -3  /* a CUDA runtime call failed; see md_last_error      */
 #define MD_ESTATE     -4  /* call order violated (e.g. md_step before state)    */
 #define MD_EOVERFLOW  -5  /* neighbour capacity exceeded and regrowth failed    */
-#define MD_EUNSTABLE  -6  /* non-finite coordinates, an atom moved more than a
-                             cell between rebuilds, or two atoms overlapped so
-                             closely that a pair force left the representable
-                             range                                            */
+#define MD_EUNSTABLE  -6  /* non-finite coordinates or velocities, or two atoms
+                             overlapped so closely that a pair force left the
+                             representable range                              */
 #define MD_ENODEV     -7  /* no usable CUDA device                              */
 
 /* ---- precision forms -------------------------------------------------- */
@@ -255,15 +254,18 @@ int md_selftest(int64_t n, int64_t failures[4]);
  *   pos  device, n x 3 doubles;  f  device, n x 3 doubles (out)
  *   pe_vir  device, 2 doubles (out): U and W = sum over pairs of r.f
  *   stream  cudaStream_t the work is queued on (NULL: legacy default
- *           stream); the call returns without synchronising it.
+ *           stream).  The call waits for its own work on that stream to
+ *           finish before it returns (it reads back a one-word flag), so f
+ *           and pe_vir are ready when it returns MD_OK.
+ * MD_EUNSTABLE when a position is not finite (f and pe_vir then hold
+ * meaningless numbers).
  * It allocates nothing: its working memory is one fixed scratch area of
  * MD_NOALLOC_SCRATCH_BYTES inside the library (a static device array that
  * every GPU which loads the library keeps until the process exits), so
  * n <= MD_NOALLOC_MAX_ATOMS and the cell count <= MD_NOALLOC_MAX_CELLS;
  * larger inputs return MD_EINVAL (message in md_last_error(NULL)).
- * The first call on a device looks up the scratch address on that device
- * (the current device); make that first call outside any stream capture.
- * All calls share the scratch area, which keeps the previous call's
+ * Every call looks up the scratch address on the current device (so a
+ * device reset between calls is harmless).  All calls share the scratch area, which keeps the previous call's
  * contents (the call clears what must start at zero): calls whose work
  * overlaps on the GPU -- on different streams or from different host
  * threads -- race and return wrong results. */

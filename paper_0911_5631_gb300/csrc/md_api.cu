@@ -455,7 +455,7 @@ struct Sim : SimBase {
         }
         if (c.error & (kErrUnstable | kErrClose)) {
             err = (c.error & kErrClose) ? "two atoms came closer than the fixed-point force range allows"
-                                        : "non-finite coordinate or an atom moved more than one cell between rebuilds";
+                                        : "non-finite coordinate or velocity";
             return MD_EUNSTABLE;
         }
         return MD_OK;

@@ -46,7 +46,7 @@ constexpr double kFixInv = 2.3283064365386963e-10;
 // Error bits recorded on the device.
 enum : int {
     kErrOverflow = 1,   // neighbour list longer than its capacity
-    kErrUnstable = 2,   // atom left its cell neighbourhood / non-finite value
+    kErrUnstable = 2,   // non-finite coordinate or velocity
     kErrClose = 4,      // pair closer than the fixed-point range allows
     kErrInternal = 8,   // a plain step node met the last step of a call
 };

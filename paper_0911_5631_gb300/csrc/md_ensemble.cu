@@ -576,7 +576,7 @@ int md_ensemble_status(md_ensemble* e, int32_t id) {
     }
     if (c.error & (kErrUnstable | kErrClose)) {
         e->err = (c.error & kErrClose) ? "two atoms came closer than the fixed-point force range allows"
-                                       : "non-finite coordinate or an atom moved more than one cell between rebuilds";
+                                       : "non-finite coordinate or velocity";
         return MD_EUNSTABLE;
     }
     return MD_OK;

@@ -163,6 +163,59 @@ __device__ __forceinline__ int wrap_add(int c, int d, int G) {
     return c;
 }
 
+// ---------------------------------------------------------------------------
+// absolute coordinates and the cell rule of Sec. 3.2 / Sec. 4.2
+// ---------------------------------------------------------------------------
+//
+// The position of an atom is defined as the FP64 number abs_coord(c, t) of
+// each component: the centre of its cell, (c + 1/2) w - L/2, plus the
+// cell-relative offset t, wrapped into [-L/2, L/2) by x - L floor((x + L/2)/L).
+// md_get_state reports exactly these numbers.  The cell of a wrapped
+// coordinate x is floor((x + L/2) G/L), folded into [0, G) (Sec. 4.2
+// truncates (r + L/2) / w the same way).  Every binning decides a cell by
+// this rule on the reported position, and the offset relative to the new
+// cell is x - centre, which is exact whenever x and the centre are within a
+// factor of two of each other (then abs_coord gives back x itself).  So
+// cell_of(md_get_state positions) equals the stored cells, element by
+// element, as the FP64 reference computes it.
+
+__device__ __forceinline__ double cell_centre(int c, double w, double hL) {
+    return __dsub_rn(__dmul_rn((double)c + 0.5, w), hL);
+}
+
+template <class P>
+__device__ __forceinline__ double abs_coord(const Args<P>& a, int d, int c, double t) {
+    const double x = __dadd_rn(cell_centre(c, a.w[d], a.hL[d]), t);
+    const double s = floor(__dmul_rn(__dadd_rn(x, a.hL[d]), a.invL[d]));
+    return __dsub_rn(x, __dmul_rn(s, a.L[d]));
+}
+
+// Cell of the wrapped coordinate x and its offset from that cell's centre.
+// An x that rounds onto the upper face belongs to cell 0 (and one below the
+// lower face to cell G - 1); its offset is then taken from the periodic
+// image next to that cell.  Returns false (cell 0, offset 0) for a
+// non-finite x and for a magnitude too large to have been wrapped.
+template <class P>
+__device__ __forceinline__ bool bin_coord(const Args<P>& a, int d, double x, int& c, double& t) {
+    if (!isfinite(x)) {
+        c = 0;
+        t = 0.0;
+        return false;
+    }
+    const double q = floor(__dmul_rn(__dadd_rn(x, a.hL[d]), a.invW[d]));
+    if (!(q >= -1.0 && q <= (double)a.G[d])) {  // a wrapped x gives q in [0, G]
+        c = 0;
+        t = 0.0;
+        return false;
+    }
+    c = (int)q;
+    double xe = x;
+    if (c >= a.G[d]) { c -= a.G[d]; xe = __dsub_rn(x, a.L[d]); }
+    if (c < 0) { c += a.G[d]; xe = __dadd_rn(x, a.L[d]); }
+    t = __dsub_rn(xe, cell_centre(c, a.w[d], a.hL[d]));
+    return true;
+}
+
 // Shift -d w of a neighbour whose 2-bit cell-offset code is k (d = k - 1).
 template <class T>
 __device__ __forceinline__ T code_shift(unsigned k, T w) {
@@ -649,9 +702,9 @@ __device__ __forceinline__ void forces_from_cells(const Args<P>& a, int i, typen
 // state load
 // ---------------------------------------------------------------------------
 
-// Wraps positions into the region, bins them (cell index as defined by
-// t = x + L/2, c = floor(t G / L), faces folded back into range) and splits
-// the offset from the cell centre into (pb, o).  Storage order = user order.
+// Wraps positions into the region, bins them by the cell rule above and
+// splits the offset from the cell centre into (pb, o).  Storage order = user
+// order.
 template <class P>
 __device__ __forceinline__ void set_state_item(const Args<P>& a, int64_t i) {
     using real = typename P::real;
@@ -663,19 +716,10 @@ __device__ __forceinline__ void set_state_item(const Args<P>& a, int64_t i) {
         double x = a.io_pos[3 * i + d];
         bad |= !isfinite(x);
         if (!isfinite(x)) x = 0.0;
-        double s = floor(__dmul_rn(__dadd_rn(x, a.hL[d]), a.invL[d]));
+        const double s = floor(__dmul_rn(__dadd_rn(x, a.hL[d]), a.invL[d]));
         x = __dsub_rn(x, __dmul_rn(s, a.L[d]));
-        double u = __dadd_rn(x, a.hL[d]);
-        int cc = (int)floor(__dmul_rn(u, a.invW[d]));
-        if (cc >= a.G[d]) { cc -= a.G[d]; u = __dsub_rn(u, a.L[d]); }
-        if (cc < 0) { cc += a.G[d]; u = __dadd_rn(u, a.L[d]); }
-        if (cc < 0 || cc >= a.G[d]) {  // only for absurd magnitudes
-            bad = true;
-            cc = 0;
-            u = 0.5 * a.w[d];
-        }
-        c[d] = cc;
-        double t = __dsub_rn(u, __dmul_rn((double)cc + 0.5, a.w[d]));
+        double t;
+        bad |= !bin_coord(a, d, x, c[d], t);
         split_offset(t, pb[d], o[d]);
         double v = a.io_vel[3 * i + d];
         bad |= !isfinite(v);
@@ -731,10 +775,11 @@ __global__ void k_clear_overflow(Counters* C) {
 // ---------------------------------------------------------------------------
 
 // Re-anchors every atom at its current position: the FP64 offset pb + o
-// becomes the new build offset (o restarts from the rounding remainder); an
-// atom whose offset left its cell moves to the adjacent cell (periodic wrap
-// is an integer operation on the cell coordinate).  Refreshes the pair
-// coordinate and counts the atoms of each cell.
+// becomes the new build offset (o restarts from the rounding remainder).  An
+// atom whose offset is not clearly inside its cell is binned afresh by the
+// cell rule above, from the position md_get_state reports (periodic wrap
+// included), and takes its offset from the new cell's centre.  Refreshes the
+// pair coordinate and counts the atoms of each cell.
 template <class P>
 __device__ __forceinline__ void bin_item(const Args<P>& a, int64_t i) {
     using real = typename P::real;
@@ -747,17 +792,14 @@ __device__ __forceinline__ void bin_item(const Args<P>& a, int64_t i) {
     double o[3];
     bool bad = false;
     for (int d = 0; d < 3; d++) {
-        double t = full_offset(pbp[d][i], op[d][i]);
+        const double t = full_offset(pbp[d][i], op[d][i]);
         split_offset(t, pb[d], o[d]);
-        // an offset clearly inside the cell needs no FP64 comparison
+        // an offset clearly inside the cell keeps it (the rule gives the same
+        // cell with a margin of 1e-6 w); NaN fails the test
         if (!(fabsf(to_f32(pb[d])) < a.hwf_in[d])) {
-            for (int it = 0; it < 2; it++) {
-                if (t >= a.hw[d]) { t = __dsub_rn(t, a.w[d]); cc[d] = wrap_add(cc[d], 1, a.G[d]); }
-                else if (t < -a.hw[d]) { t = __dadd_rn(t, a.w[d]); cc[d] = wrap_add(cc[d], -1, a.G[d]); }
-            }
-            bad |= !(t >= -a.hw[d] && t < a.hw[d]);  // also catches NaN
-            if (!(t >= -a.hw[d] && t < a.hw[d])) t = 0.0;
-            split_offset(t, pb[d], o[d]);
+            double tn;
+            bad |= !bin_coord(a, d, abs_coord(a, d, cc[d], t), cc[d], tn);
+            split_offset(tn, pb[d], o[d]);
         }
         pbp[d][i] = pb[d];
         op[d][i] = o[d];
@@ -996,17 +1038,29 @@ __global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
     commit_item<P>(a, s);
 }
 
-// Exact FP64 neighbour criterion r^2 < r_n^2 on the cell-relative offsets
-// (no contraction, fixed operation order).
+// Exact FP64 neighbour criterion r^2 < r_n^2 for atom i in cell ci and atom
+// j in the stencil cell ci + d, evaluated as the FP64 reference evaluates
+// its cell pairs (Sec. 3.2): e = (x_i - x_j) + s L on the reported absolute
+// coordinates, s = -1 / +1 when ci + d wraps across the upper / lower face,
+// r^2 = (e_x^2 + e_y^2) + e_z^2, every operation rounded, no contraction.
 template <class P>
-__device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int dx, int dy, int dz) {
-    double ex = __dadd_rn(__dsub_rn(full_offset(a.pbx[i], a.ox[i]), full_offset(a.pbx[j], a.ox[j])),
-                          __dmul_rn(-(double)dx, a.w[0]));
-    double ey = __dadd_rn(__dsub_rn(full_offset(a.pby[i], a.oy[i]), full_offset(a.pby[j], a.oy[j])),
-                          __dmul_rn(-(double)dy, a.w[1]));
-    double ez = __dadd_rn(__dsub_rn(full_offset(a.pbz[i], a.oz[i]), full_offset(a.pbz[j], a.oz[j])),
-                          __dmul_rn(-(double)dz, a.w[2]));
-    double r2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+__device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int cx, int cy, int cz, int dx, int dy,
+                                            int dz) {
+    const int ci[3] = {cx, cy, cz}, dd[3] = {dx, dy, dz};
+    const typename P::real* pb[3] = {a.pbx, a.pby, a.pbz};
+    const double* o[3] = {a.ox, a.oy, a.oz};
+    double e[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        int cj = ci[k] + dd[k];
+        double s = 0.0;
+        if (cj >= a.G[k]) { cj -= a.G[k]; s = -1.0; }
+        else if (cj < 0) { cj += a.G[k]; s = 1.0; }
+        const double xi = abs_coord(a, k, ci[k], full_offset(pb[k][i], o[k][i]));
+        const double xj = abs_coord(a, k, cj, full_offset(pb[k][j], o[k][j]));
+        e[k] = __dadd_rn(__dsub_rn(xi, xj), __dmul_rn(s, a.L[k]));
+    }
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
     return r2 < a.rn2;
 }
 
@@ -1087,7 +1141,7 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
                     const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
                     const int j = __float_as_int(pj.w);
                     bool take = rr < lo2;
-                    if (!take && rr < hi2) take = within_rn_fp64(a, i, j, k - 1, dy, dz);
+                    if (!take && rr < hi2) take = within_rn_fp64(a, i, j, cx, cy, cz, k - 1, dy, dz);
                     take = take && t != self;
                     if constexpr (kSort) {
                         if (take && m < kBuildStage) stage[m * stride] = make_int2(j | code, __float_as_int(rr));
@@ -1599,11 +1653,7 @@ __global__ void __launch_bounds__(kBlock) k_get_state(Args<P> a) {
     const double* o[3] = {a.ox, a.oy, a.oz};
     const typename P::vel* v[3] = {a.vx, a.vy, a.vz};
     for (int d = 0; d < 3; d++) {
-        double centre = __dsub_rn(__dmul_rn((double)cc[d] + 0.5, a.w[d]), a.hL[d]);
-        double x = __dadd_rn(centre, full_offset(pb[d][i], o[d][i]));
-        double s = floor(__dmul_rn(__dadd_rn(x, a.hL[d]), a.invL[d]));
-        x = __dsub_rn(x, __dmul_rn(s, a.L[d]));
-        a.io_pos[3 * (int64_t)u + d] = x;
+        a.io_pos[3 * (int64_t)u + d] = abs_coord(a, d, cc[d], full_offset(pb[d][i], o[d][i]));
         if constexpr (P::kFp64) a.io_vel[3 * (int64_t)u + d] = v[d][i];
         else a.io_vel[3 * (int64_t)u + d] = cvt::f64(v[d][i]);
     }

@@ -17,7 +17,6 @@
 
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "../../include/md.h"
@@ -43,7 +42,8 @@ constexpr size_t kOffRank = kOffCell + sizeof(int) * kMaxAtoms;            // in
 constexpr size_t kOffOrder = kOffRank + sizeof(int) * kMaxAtoms;           // int[kMaxAtoms]
 constexpr size_t kOffPart = kOffOrder + sizeof(int) * kMaxAtoms;           // double[2 kMaxBlocks]
 constexpr size_t kOffPos = (kOffPart + sizeof(double) * 2 * kMaxBlocks + 255) & ~size_t(255);  // double4[kMaxAtoms]
-constexpr size_t kScratchBytes = kOffPos + sizeof(double) * 4 * kMaxAtoms;
+constexpr size_t kOffFlag = kOffPos + sizeof(double) * 4 * kMaxAtoms;     // int: a non-finite input was seen
+constexpr size_t kScratchBytes = kOffFlag + 256;
 static_assert(kScratchBytes <= MD_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds the declared size");
 
 __device__ __align__(256) unsigned char g_scratch[MD_NOALLOC_SCRATCH_BYTES];
@@ -63,6 +63,7 @@ struct Scratch {
     int* order;
     double* part;
     double* pos;  // x, y, z, index per atom in cell order
+    int* bad;     // set when a position is not finite
 };
 
 __device__ __forceinline__ int gid() { return blockIdx.x * blockDim.x + threadIdx.x; }
@@ -83,16 +84,20 @@ __device__ __forceinline__ int wrap_bin(double& x, const Geo& g, int d) {
 
 __global__ void nz_zero(Geo g, Scratch s) {
     for (int c = gid(); c < g.ncells; c += gridDim.x * blockDim.x) s.count[c] = 0;
+    if (gid() == 0) *s.bad = 0;
 }
 
 __global__ void nz_bin(Geo g, Scratch s, const double* __restrict__ pos) {
     int i = gid();
     if (i >= g.n) return;
     int c[3];
+    bool finite = true;
     for (int d = 0; d < 3; d++) {
         double x = pos[3 * (size_t)i + d];
+        finite = finite && isfinite(x);
         c[d] = wrap_bin(x, g, d);
     }
+    if (!finite) atomicExch(s.bad, 1);
     int cl = (c[2] * g.G[1] + c[1]) * g.G[0] + c[0];
     s.cell[i] = cl;
     s.rank[i] = atomicAdd(&s.count[cl], 1);
@@ -258,28 +263,23 @@ __global__ void nz_reduce(int nblocks, Scratch s, double* __restrict__ out) {
     }
 }
 
-// Per-device address of g_scratch, looked up once per device.
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_addr[kMaxDevices] = {};
+// Address of g_scratch on the current device.  Looked up on every call (a
+// cheap query): a cached address would go stale if the caller reset the
+// device and the module were loaded again.
 int scratch_for_current_device(void** out) {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) {
         cudaGetLastError();
         md::set_call_error("no current CUDA device");
         return MD_ENODEV;
     }
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            md::set_call_error((std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
-            return MD_ECUDA;
-        }
-        g_addr[dev] = p;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        md::set_call_error((std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
+        return MD_ECUDA;
     }
-    *out = g_addr[dev];
+    *out = p;
     return MD_OK;
 }
 
@@ -342,6 +342,7 @@ extern "C" int md_forces_noalloc(const double box[3], int64_t n, double rc, doub
     s.order = (int*)(b + kOffOrder);
     s.part = (double*)(b + kOffPart);
     s.pos = (double*)(b + kOffPos);
+    s.bad = (int*)(b + kOffFlag);
 
     cudaStream_t st = (cudaStream_t)stream;
     int ga = (g.n + kThreads - 1) / kThreads;
@@ -358,6 +359,19 @@ extern "C" int md_forces_noalloc(const double box[3], int64_t n, double rc, doub
     if (e != cudaSuccess) {
         md::set_call_error((std::string("launch: ") + cudaGetErrorString(e)).c_str());
         return MD_ECUDA;
+    }
+    // the non-finite check: a 4-byte read of the flag into this stack
+    // variable, after the call's own work on the stream
+    int bad = 0;
+    e = cudaMemcpyAsync(&bad, s.bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        md::set_call_error((std::string("flag read: ") + cudaGetErrorString(e)).c_str());
+        return MD_ECUDA;
+    }
+    if (bad) {
+        md::set_call_error("non-finite position");
+        return MD_EUNSTABLE;
     }
     return MD_OK;
 }

@@ -6,7 +6,8 @@ import numpy as np
 import pytest
 
 import paper_0911_5631_gb300 as md
-from mdcheck import DT, RC, ensure_built, sim, state
+import oracle
+from mdcheck import DT, RC, assert_trajectory_matches, ensure_built, sim, state
 
 pytestmark = pytest.mark.gpu
 
@@ -66,6 +67,34 @@ def test_replica_matches_md_step_bitwise(case):
     # both sum KE, PE and W in FP64, in different fixed orders
     for k in ("ke", "pe", "virial"):
         assert abs(m0[k] - m1[k]) <= 1e-12 * abs(m0[k]), (k, m0[k], m1[k])
+
+
+def test_replicas_match_oracle():
+    # Replicas of different N, rho and T, through md_ensemble_run in one
+    # launch, each against the FP64 oracle run from the same state: single
+    # blocks for the small ones, thread-block clusters of 4 for those of at
+    # least 3000 atoms.
+    specs = [(256, 0.8, 1.0, 31), (700, 0.6, 0.7, 32), (1500, 1.0, 2.0, 33), (3000, 0.9, 1.2, 34),
+             (5324, 0.7, 0.5, 35), (8788, 0.8, 1.5, 36)]
+    k = 60
+    with md.Ensemble(ARENA) as e:
+        e.set_shape(1024, 0, 4, 3000)
+        ids, starts = [], []
+        for n, rho, T, seed in specs:
+            pos, vel, L = _state(n, rho, T, seed)
+            ids.append(e.add(pos, vel, L, RC, 0.4, DT, reorder_interval=20))
+            starts.append((pos, vel, L))
+        e.run(ids, [k] * len(ids))
+        e.sync()
+        for rid, (pos, vel, L), (n, rho, T, seed) in zip(ids, starts, specs):
+            assert e.status(rid) == md.MD_OK
+            p, v = e.get_state(rid)
+            m = e.measure(rid)
+            assert m["step"] == k and m["rebuilds"] >= 1, (n, m["rebuilds"])
+            ref = oracle.run(oracle.wrap(pos, L), vel, L, RC, 0.4, DT, k)
+            assert_trajectory_matches(p, v, ref, L, "mixed", k)
+            e_ref = ref["ke"][-1] + ref["pe"][-1]
+            assert m["ke"] + m["pe"] == pytest.approx(e_ref, rel=1e-5), n
 
 
 def _mix(e, rng, count):

@@ -5,7 +5,8 @@ import numpy as np
 import pytest
 
 import oracle
-from mdcheck import DT, FORCE_TOL, RC, ensure_built, rel_rms, sim, state
+from mdcheck import (DT, FORCE_TOL, RC, assert_same_cells, assert_same_pairs, ensure_built, oracle_grid, rel_rms,
+                     sim, state)
 from paper_0911_5631_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -41,16 +42,21 @@ def test_one_million_atoms(prec):
     p, v, f = _sampled_force_check(s, L, prec)
     # momentum: zero at start, conserved up to rounding
     assert np.abs(v.sum(axis=0)).max() < (1e-2 if prec == "mixed" else 1e-8)
-    # exact neighbour sets of sampled atoms after a fresh build here
-    s.set_state(p, v)
+    # the next in-trajectory rebuild (incremental re-binning, list rebuilt in
+    # place, no reload): every cell and the whole pair set against the
+    # reference on the positions of that moment
+    G = np.array(s.plan()["G"])
+    last = m["rebuilds"]
+    for _ in range(40):
+        s.step(1)
+        if s.measure()["rebuilds"] > last:
+            break
+    assert s.measure()["rebuilds"] == last + 1
+    p, v = s.get_state()
+    assert_same_cells(s.cells(), p, L, G)
     pairs, entries = s.neighbor_pairs()
     rn = RC + cfg["skin"]
-    for i in np.random.default_rng(1).choice(cfg["n"], 12, replace=False):
-        mine = np.sort(np.concatenate([pairs[pairs[:, 0] == i, 1], pairs[pairs[:, 1] == i, 0]]))
-        ref = oracle.neighbors_of(p, L, rn, i)
-        diff = set(mine.tolist()) ^ set(ref.tolist())
-        for j in diff:
-            assert abs(oracle.pair_r2(p, L, i, j) - rn * rn) < 1e-10
+    assert_same_pairs(pairs, oracle.pairs_cells(p, L, oracle_grid(L, rn), rn), p, L, rn)
     assert entries == 2 * len(pairs)
     assert 11.0 < entries / cfg["n"] < 13.0  # N_p / N_a near 12 for this state
     s.close()

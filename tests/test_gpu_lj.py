@@ -43,7 +43,8 @@ def test_lj_forces_pairs_energy(rc, prec):
     assert m["virial"] == pytest.approx(W, rel=10 * FORCE_TOL[prec], abs=1e-9 * abs(U))
     rn = rc + SKIN
     pairs, entries = s.neighbor_pairs()
-    assert_same_pairs(pairs, oracle.pairs_cells(pw, L, oracle_grid(L, rn), rn), pw, L, rn)
+    p, _ = s.get_state()
+    assert_same_pairs(pairs, oracle.pairs_cells(p, L, oracle_grid(L, rn), rn), p, L, rn)
     nbar = 4.0 / 3.0 * np.pi * rn ** 3 * RHO
     assert entries / n == pytest.approx(nbar, rel=0.2)  # about (4/3) pi r_n^3 rho neighbours
     s.close()

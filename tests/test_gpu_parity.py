@@ -6,8 +6,8 @@ import pytest
 
 import oracle
 import paper_0911_5631_gb300 as md
-from mdcheck import (DT, FORCE_TOL, RC, assert_same_pairs, ensure_built, min_image, oracle_grid,
-                     rel_rms, sim, state)
+from mdcheck import (DT, FORCE_TOL, RC, assert_same_cells, assert_same_pairs, ensure_built, min_image,
+                     oracle_grid, rel_rms, sim, state, trajectory_tol)
 
 pytestmark = pytest.mark.gpu
 
@@ -40,10 +40,16 @@ def _setup(case, prec, **kw):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_cells_bit_exact(case, prec):
+    # the load bins the wrapped input by the reference's rule; the positions
+    # the GPU then reports are the wrapped input (an atom whose offset from
+    # its cell centre is not exact in FP64 may move by an ulp)
     s, pos, vel, L, skin = _setup(case, prec)
     G = np.array(s.plan()["G"])
     pw = oracle.wrap(pos, L)
+    p, _ = s.get_state()
+    assert np.abs(p - pw).max() <= 4e-16 * np.max(L)
     assert np.array_equal(s.cells(), oracle.cell_of(pw, L, G))
+    assert_same_cells(s.cells(), p, L, G)
     m = s.measure()
     counts = np.bincount(oracle.cell_of(pw, L, G), minlength=int(np.prod(G)))
     assert m["max_occupancy"] == counts.max()
@@ -53,15 +59,55 @@ def test_cells_bit_exact(case, prec):
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_neighbor_pairs_match_oracle(case, prec):
+    # identical sets: the GPU decides the pairs near r_n by the reference's
+    # own FP64 expression on the positions it reports
     s, pos, vel, L, skin = _setup(case, prec)
-    pw = oracle.wrap(pos, L)
+    p, _ = s.get_state()
     rn = RC + skin
     pairs, entries = s.neighbor_pairs()
     assert entries == 2 * len(pairs)  # full list: every pair in both columns
-    ref = oracle.pairs_cells(pw, L, oracle_grid(L, rn), rn)
-    assert_same_pairs(pairs, ref, pw, L, rn)
+    assert_same_pairs(pairs, oracle.pairs_cells(p, L, oracle_grid(L, rn), rn), p, L, rn)
+    pw = oracle.wrap(pos, L)
+    assert_same_pairs(pairs, oracle.pairs_cells(pw, L, oracle_grid(L, rn), rn), pw, L, rn)
     m = s.measure()
     assert m["list_entries"] == entries
+    s.close()
+
+
+def _check_rebuilt_state(s, L, skin, G):
+    """Cells and neighbour pairs of the last rebuild against the reference,
+    from the positions the GPU reports (the rebuild's own positions when the
+    last step rebuilt)."""
+    p, _ = s.get_state()
+    assert_same_cells(s.cells(), p, L, G)
+    rn = RC + skin
+    pairs, entries = s.neighbor_pairs()
+    assert entries == 2 * len(pairs)
+    assert_same_pairs(pairs, oracle.pairs_cells(p, L, oracle_grid(L, rn), rn), p, L, rn)
+    return len(pairs)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("case", CASES, ids=IDS)
+def test_rebuilds_along_trajectory_match_oracle(case, prec):
+    # The rebuilds of md_step re-bin atoms incrementally (k_bin) and rebuild
+    # the lists in place, with periodic reorders; right after every step
+    # that rebuilt, the stored cells and the list must be the reference's
+    # for the positions of that moment.  No md_set_state in between.
+    pos, vel, L, skin = _fluid(case)
+    s = sim(pos, vel, L, skin=skin, precision=prec, reorder_interval=15)
+    G = np.array(s.plan()["G"])
+    seen, last, steps = 0, s.measure()["rebuilds"], 0
+    while seen < 4 and steps < 400:
+        s.step(1)
+        steps += 1
+        m = s.measure()
+        if m["rebuilds"] > last:
+            last = m["rebuilds"]
+            seen += 1
+            _check_rebuilt_state(s, L, skin, G)
+    assert seen == 4
+    assert s.measure()["reorders"] >= 2  # the load's reorder and at least one more
     s.close()
 
 
@@ -110,12 +156,7 @@ def test_newton_third_law_in_result(prec):
     s.close()
 
 
-def _trajectory_tol(prec, f_rms, k):
-    # velocity error after k steps from the same state: k dt times the force
-    # error allowed per step, with a factor 10 for growth along the segment
-    fe = FORCE_TOL[prec] * f_rms
-    dv = 10.0 * k * DT * fe + (1e-7 if prec == "mixed" else 1e-14)
-    return dv, k * DT * dv + 1e-13
+_trajectory_tol = trajectory_tol
 
 
 def _fluid(case):

@@ -7,7 +7,8 @@ import pytest
 import paper_0911_5631_gb300 as md
 from paper_0911_5631_gb300 import inputs
 from paper_0911_5631_gb300.serve import Request, Server
-from mdcheck import DT, RC, ensure_built, sim
+import oracle
+from mdcheck import DT, RC, assert_trajectory_matches, ensure_built, sim
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +52,11 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
         p, v = _alone(r)
         assert np.array_equal(r.result[0], p), r.key
         assert np.array_equal(r.result[1], v), r.key
+    # the smallest request (an ensemble replica) and the largest (its own
+    # handle) against the FP64 oracle from the request's start
+    for r in (min(reqs, key=lambda q: q.atoms), max(reqs, key=lambda q: q.atoms)):
+        ref = oracle.run(oracle.wrap(r.pos, r.box), r.vel, r.box, RC, 0.4, DT, r.nsteps, record=False)
+        assert_trajectory_matches(r.result[0], r.result[1], ref, r.box, "mixed", r.nsteps)
 
 
 def test_admission_waits_for_space():

@@ -126,10 +126,13 @@ def _as_set(pairs):
     return set(map(tuple, np.asarray(pairs).tolist()))
 
 
-def _assert_same_pairs(a, b, pos, L, rcut, tol=1e-12):
+def _assert_same_pairs(a, b, pos, L, rcut):
+    # The minimum-image separation d - L round(d / L) is, bit for bit, the
+    # cell pair's (x_i - x_j) + s L: round(d / L) is the same -1, 0 or 1 as s,
+    # and the product with L is exact.  So the two sets must be identical.
     sa, sb = _as_set(a), _as_set(b)
-    for (i, j) in sa ^ sb:  # only pairs within rounding of the cutoff may differ
-        assert abs(oracle.pair_r2(pos, L, i, j) - rcut * rcut) < tol, (i, j)
+    diff = sorted(sa ^ sb)
+    assert not diff, [(i, j, oracle.pair_r2(pos, L, i, j) - rcut * rcut) for (i, j) in diff[:10]]
 
 
 CASES = [
@@ -318,3 +321,35 @@ def test_table4_with_the_papers_protocol():
     e_kin = out["ke"][1001:2001].mean() / n
     assert e_kin == pytest.approx(g["e_kin"], abs=0.003)
     assert e_tot == pytest.approx(g["e_tot"], abs=0.004)
+
+
+# --------------------------------------------------------------------------
+# The threaded build (timing only) against the plain build
+# --------------------------------------------------------------------------
+
+def test_threaded_build_matches_plain_build():
+    # Same source, compiled with OpenMP: the cell range and the pair list are
+    # cut into one chunk per thread and joined in order, so the pair list is
+    # the same list; only the order of the force sums differs, which moves
+    # forces and a short trajectory by rounding alone (1e-12).
+    assert oracle.threads(threaded=False) == 1
+    pos, vel, L = inputs.wca_state(4000, 0.8, 1.0, 21, jitter_amp=0.15)
+    pos = oracle.wrap(pos, L)
+    rn = RC + 0.4
+    G, ok = oracle.cell_grid(L, rn)
+    a = oracle.pairs_cells(pos, L, G, rn)
+    b = oracle.pairs_cells(pos, L, G, rn, threaded=True)
+    assert np.array_equal(a, b)  # the same pairs in the same order
+    Gc, _ = oracle.cell_grid(L, RC)
+    f0, u0, w0 = oracle.forces_cells(pos, L, Gc, RC, 1.0)
+    f1, u1, w1 = oracle.forces_cells(pos, L, Gc, RC, 1.0, threaded=True)
+    assert np.sqrt(np.mean((f1 - f0) ** 2)) <= 1e-12 * np.sqrt(np.mean(f0 ** 2))
+    assert u1 == pytest.approx(u0, rel=1e-12) and w1 == pytest.approx(w0, rel=1e-12)
+    melt = oracle.run(pos, vel, L, RC, 0.4, 0.005, 200, record=False)
+    r0 = oracle.run(melt["pos"], melt["vel"], L, RC, 0.4, 0.005, 30)
+    r1 = oracle.run(melt["pos"], melt["vel"], L, RC, 0.4, 0.005, 30, threaded=True)
+    assert r0["nrebuild"] == r1["nrebuild"] and r0["npairs_sum"] == r1["npairs_sum"]
+    scale = np.sqrt(np.mean(r0["vel"] ** 2))
+    assert np.sqrt(np.mean((r1["vel"] - r0["vel"]) ** 2)) <= 1e-12 * scale
+    assert np.abs(r1["pos"] - r0["pos"]).max() <= 1e-12 * np.max(L)
+    assert np.abs(r1["pe"] - r0["pe"]).max() <= 1e-12 * np.abs(r0["pe"]).max()
