@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="wca_fcc64_n1m")
-    ap.add_argument("--chunk", type=int, default=100, help="MD steps per benchmark step")
+    ap.add_argument("--chunk", type=int, default=500,
+                    help="MD steps per benchmark step (five reorder intervals)")
     ap.add_argument("--equil", type=int, default=1000, help="untimed equilibration MD steps")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -139,7 +140,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
 
@@ -172,8 +173,24 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def _oracle_rate(oracle, pos, vel, L, cfg, threaded, seconds):
+    """atom-steps/s of one oracle build on a bounded sample: a 2-step probe
+    sizes the sample to about `seconds`, then one run is timed (it includes
+    the initial list build).  Returns (value, steps, seconds taken)."""
+    n = pos.shape[0]
+    t0 = time.perf_counter()
+    oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, 2, record=False, threaded=threaded)
+    t1 = time.perf_counter() - t0
+    steps = int(max(4, min(2000, seconds / max(t1 / 2, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, steps, record=False, threaded=threaded)
+    t = time.perf_counter() - t0
+    return n * steps / t, steps, t
+
+
 def run_reference(args):
-    """Times the FP64 CPU oracle on the host cores."""
+    """Times the FP64 CPU oracle on the host cores (the OpenMP build of the
+    oracle source, every core)."""
     import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -182,12 +199,13 @@ def run_reference(args):
     n = cfg["n"]
     pos, vel, L = inputs.wca_state(n, cfg["rho"], cfg["T"], cfg["seed"])
     pos = oracle.wrap(pos, L)
+    cores = oracle.threads(True)
     sample = 4  # MD steps per benchmark step, from the lattice start
     for _ in range(args.warmup):
-        oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, sample, record=False)
+        oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, sample, record=False, threaded=True)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, sample, record=False)
+        oracle.run(pos, vel, L, cfg.get("rc", RC), cfg["skin"], DT, sample, record=False, threaded=True)
     t = time.perf_counter() - t0
     value = n * sample * args.steps / t
     line = {
@@ -197,29 +215,31 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": args.workload, "n_atoms": n, "rho": cfg["rho"],
                                         "T": cfg["T"], "skin": cfg["skin"],
                                         "md_steps_per_bench_step": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d MD steps of the %d-atom workload from its lattice start per "
-                                   "benchmark step, single-threaded C oracle" % (sample, n)},
+                                   "benchmark step, C oracle built with OpenMP on %d threads"
+                                   % (sample, n, cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(pos, vel, L, cfg, seconds=15.0):
-    """The oracle as it stands, single-threaded, on a bounded sample."""
+def cpu_baseline(pos, vel, L, cfg, seconds=10.0):
+    """The oracle as it stands on the host cores, each build on a bounded
+    sample of the equilibrated state: the plain single-threaded build (the
+    parity reference) and the OpenMP build of the same source on every
+    core.  `value` and `cores` are the all-core figures."""
     import oracle
     n = pos.shape[0]
     p = oracle.wrap(pos, L)
-    t0 = time.perf_counter()
-    oracle.run(p, vel, L, cfg.get("rc", RC), cfg["skin"], DT, 2, record=False)
-    t1 = time.perf_counter() - t0
-    steps = int(max(4, min(400, seconds / max(t1 / 2, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.run(p, vel, L, cfg.get("rc", RC), cfg["skin"], DT, steps, record=False)
-    t = time.perf_counter() - t0
-    return {"value": n * steps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+    v1, k1, t1 = _oracle_rate(oracle, p, vel, L, cfg, False, seconds)
+    vt, kt, tt = _oracle_rate(oracle, p, vel, L, cfg, True, seconds)
+    cores = oracle.threads(True)
+    return {"value": vt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d MD steps of the %d-atom equilibrated state (includes the initial list build), "
-                      "single-threaded C oracle, %.1f s" % (steps, n, t)}
+                      "C oracle built with OpenMP on %d threads, %.1f s" % (kt, n, cores, tt),
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": "%d MD steps, plain single-threaded C oracle, %.1f s" % (k1, t1)}}
 
 
 def ensemble_bench(md, torch, stream, device, replicas, steps, probe):

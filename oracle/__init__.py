@@ -19,6 +19,11 @@ arXiv 0911.5631:
 * ``forces_cells`` / ``forces_brute`` / ``forces_sampled`` -- forces, U, W
 * ``run``             -- the step loop (a)-(f) of Sec. 3.1 with a skin-based
                          neighbour list and the delta/2 rebuild rule
+
+Two builds of the one source: ``liboracle.so`` (plain, single threaded) is
+the parity reference every check uses; ``liboracle_omp.so`` (the same code
+compiled with OpenMP) only times the oracle on all host cores
+(``run(..., threaded=True)``); a CPU test pins it to the plain build.
 """
 from __future__ import annotations
 
@@ -32,18 +37,27 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "md_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 CFLAGS = ["-O2", "-std=c11", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared"]
 
 
-def build(force: bool = False) -> str:
-    """Compile md_oracle.c into liboracle.so beside it (gcc, no contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
+def _build_one(path, extra, force):
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False, threaded: bool = True) -> str:
+    """Compile md_oracle.c into liboracle.so beside it (gcc, no contraction)
+    and, with threaded, also into liboracle_omp.so (-fopenmp)."""
+    _build_one(_LIB, [], force)
+    if threaded:
+        _build_one(_LIB_OMP, ["-fopenmp"], force)
     return _LIB
 
 
@@ -61,12 +75,12 @@ class _Params(C.Structure):
     ]
 
 
-def _load():
-    global _lib
+def _load(threaded: bool = False):
     with _lock:
-        if _lib is not None:
-            return _lib
-        lib = C.CDLL(build())
+        if threaded in _libs:
+            return _libs[threaded]
+        lib = C.CDLL(_build_one(_LIB_OMP, ["-fopenmp"], False) if threaded else _build_one(_LIB, [], False))
+        lib.orc_threads.restype = C.c_int
         d, i64, i32 = C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int32)
         lib.orc_pair.argtypes = [C.c_double, C.c_double, d, d]
         lib.orc_cell_grid.argtypes = [d, C.c_double, C.c_int, C.POINTER(C.c_int)]
@@ -89,8 +103,14 @@ def _load():
         lib.orc_run.argtypes = [i64, d, d, C.POINTER(_Params), i64, d, d, d, d,
                                 C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         lib.orc_run.restype = C.c_int
-        _lib = lib
+        _libs[threaded] = lib
         return lib
+
+
+def threads(threaded: bool = True) -> int:
+    """Threads the (threaded) oracle runs on: OMP_NUM_THREADS, else all host
+    cores; 1 for the plain build."""
+    return int(_load(threaded).orc_threads())
 
 
 def _dp(a):
@@ -162,10 +182,10 @@ def _pairs(fn, *args, n_hint):
         cap = int(m)
 
 
-def pairs_cells(pos, L, G, rcut):
+def pairs_cells(pos, L, G, rcut, threaded=False):
     """Pairs (i < j) within rcut via the half-shell cell enumeration; the
     positions must already be wrapped into the region."""
-    lib = _load()
+    lib = _load(threaded)
     p, L = _pos(pos), _box(L)
     Gc = (C.c_int * 3)(*[int(g) for g in G])
     return _pairs(lib.orc_pairs_cells, p.shape[0], _dp(p), _dp(L), Gc, float(rcut),
@@ -185,9 +205,9 @@ def pair_r2(pos, L, i, j):
     return lib.orc_pair_r2(_dp(p), _dp(L), int(i), int(j))
 
 
-def forces_cells(pos, L, G, rc, ushift):
+def forces_cells(pos, L, G, rc, ushift, threaded=False):
     """(f, U, W) from the cell-list pair set within rc (Newton's third law)."""
-    lib = _load()
+    lib = _load(threaded)
     p, L = _pos(pos), _box(L)
     Gc = (C.c_int * 3)(*[int(g) for g in G])
     f = np.empty_like(p)
@@ -236,12 +256,13 @@ def neighbors_of(pos, L, rcut, i):
 
 
 def run(pos, vel, L, rc, skin, dt, nsteps, ushift=None, even_cells=False, rescale_every=0,
-        rescale_until=0, T_target=1.0, record=True):
+        rescale_until=0, T_target=1.0, record=True, threaded=False):
     """Run the reference MD loop.  Returns a dict with the final (wrapped)
     positions, velocities and forces, per-step KE/PE/W arrays (index 0 is the
     initial state), the number of rebuilds after the initial build and the
-    summed pair-list length over all builds."""
-    lib = _load()
+    summed pair-list length over all builds.  threaded: the OpenMP build
+    (timing only; the same pair lists, force sums in another order)."""
+    lib = _load(threaded)
     p = _pos(pos).copy()
     v = np.ascontiguousarray(vel, dtype=np.float64).copy()
     assert v.shape == p.shape

@@ -8,7 +8,16 @@
  * shares no code, header, table or constant generator with the CUDA path.
  *
  * Everything is double precision, compiled without FP contraction
- * (-ffp-contract=off), single threaded, in the order the paper states:
+ * (-ffp-contract=off), in the order the paper states.  The parity reference
+ * is the plain single-threaded build.  The same source compiled with
+ * -fopenmp gives the threaded build that only times the oracle on all host
+ * cores: the cell loop of the pair enumeration and the pair loop of the
+ * forces are cut into as many contiguous chunks as there are threads, and
+ * the chunks' results are joined in chunk order (pair lists concatenated,
+ * force arrays and sums added chunk by chunk), so with one chunk both builds
+ * are the same program and with several the pair list is the same list and
+ * only the order of the force sums differs.
+ *
  *
  *   - pair potential: Eq. (1) (Lennard-Jones) truncated at r_c, plus a
  *     constant shift; the soft-sphere (SP, WCA) case is r_c = 2^(1/6) with a
@@ -35,6 +44,26 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Number of chunks the two big loops are cut into: the threads of the
+ * threaded build, 1 otherwise. */
+static int n_chunks(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Number of threads the oracle runs on (1 in the plain build). */
+int orc_threads(void)
+{
+    return n_chunks();
+}
 
 /* ------------------------------------------------------------------ */
 /* Pair term                                                           */
@@ -77,6 +106,7 @@ void orc_wrap(int64_t n, double* pos, const double L[3])
     for (int d = 0; d < 3; d++) {
         double hL = 0.5 * L[d];
         double invL = 1.0 / L[d];
+#pragma omp parallel for schedule(static)
         for (int64_t i = 0; i < n; i++) {
             double x = pos[3 * i + d];
             double s = floor((x + hL) * invL);
@@ -152,33 +182,15 @@ static const int HALF_SHELL[14][3] = {
     {0, 0, 1},  {1, 0, 1},  {1, 1, 1},  {0, 1, 1},  {-1, 1, 1},
     {-1, 0, 1}, {-1, -1, 1}, {0, -1, 1}, {1, -1, 1}};
 
-/* Linked-list cell assignment and half-shell pair enumeration with cutoff
- * rcut (Sec. 3.2).  Positions must lie in [-L/2, L/2).  Each pair with
+/* The pairs of the cells c1 in [c_beg, c_end) with the cells of their half
+ * shell, given the linked lists head/next (Sec. 3.2).  Each pair with
  * |r_i - r_j + b| < rcut is recorded once together with its shift b. */
-static int build_pairs_cells(int64_t n, const double* pos, const double L[3], const int G[3],
-                             double rcut, pairlist_t* pl)
+static int pairs_of_cells(const double* pos, const double L[3], const int G[3], const int32_t* head,
+                          const int32_t* next, double rcut, int64_t c_beg, int64_t c_end, pairlist_t* pl)
 {
-    int64_t nc = (int64_t)G[0] * G[1] * G[2];
-    int32_t* head = (int32_t*)malloc((size_t)nc * sizeof(int32_t));
-    int32_t* next = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
-    int32_t* cell = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
-    if (!head || !next || !cell) {
-        free(head); free(next); free(cell);
-        return -1;
-    }
-    for (int64_t c = 0; c < nc; c++) head[c] = -1;
-    orc_cell_of(n, pos, L, G, cell);
-    for (int64_t i = 0; i < n; i++) {
-        next[i] = head[cell[i]];
-        head[cell[i]] = (int32_t)i;
-    }
     double rc2 = rcut * rcut;
-    pl->n = 0;
-    int rc_err = 0;
-    for (int cz = 0; cz < G[2] && !rc_err; cz++)
-    for (int cy = 0; cy < G[1] && !rc_err; cy++)
-    for (int cx = 0; cx < G[0] && !rc_err; cx++) {
-        int32_t c1 = (cz * G[1] + cy) * G[0] + cx;
+    for (int64_t c1 = c_beg; c1 < c_end; c1++) {
+        int cx = (int)(c1 % G[0]), cy = (int)((c1 / G[0]) % G[1]), cz = (int)(c1 / ((int64_t)G[0] * G[1]));
         for (int k = 0; k < 14; k++) {
             int cc[3] = {cx + HALF_SHELL[k][0], cy + HALF_SHELL[k][1], cz + HALF_SHELL[k][2]};
             int s[3];
@@ -199,16 +211,63 @@ static int build_pairs_cells(int64_t n, const double* pos, const double L[3], co
                     double dz = pos[3 * i1 + 2] - pos[3 * i2 + 2] + s[2] * L[2];
                     double r2 = dx * dx + dy * dy + dz * dz;
                     if (r2 < rc2) {
-                        if (pl_push(pl, i1, i2, s)) { rc_err = 1; break; }
+                        if (pl_push(pl, i1, i2, s)) return -1;
                     }
                 }
-                if (rc_err) break;
             }
-            if (rc_err) break;
         }
     }
-    free(head); free(next); free(cell);
-    return rc_err ? -1 : 0;
+    return 0;
+}
+
+/* Linked-list cell assignment and half-shell pair enumeration with cutoff
+ * rcut (Sec. 3.2), cells taken in the order c = (c_z G_y + c_y) G_x + c_x.
+ * Positions must lie in [-L/2, L/2).  The cell range is cut into n_chunks()
+ * contiguous pieces whose lists are concatenated in order, which is the
+ * list one pass over all cells makes. */
+static int build_pairs_cells(int64_t n, const double* pos, const double L[3], const int G[3],
+                             double rcut, pairlist_t* pl)
+{
+    int64_t nc = (int64_t)G[0] * G[1] * G[2];
+    int32_t* head = (int32_t*)malloc((size_t)nc * sizeof(int32_t));
+    int32_t* next = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int32_t* cell = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    int nch = n_chunks();
+    pairlist_t* part = (pairlist_t*)calloc((size_t)nch, sizeof(pairlist_t));
+    if (!head || !next || !cell || !part) {
+        free(head); free(next); free(cell); free(part);
+        return -1;
+    }
+    for (int64_t c = 0; c < nc; c++) head[c] = -1;
+    orc_cell_of(n, pos, L, G, cell);
+    for (int64_t i = 0; i < n; i++) {
+        next[i] = head[cell[i]];
+        head[cell[i]] = (int32_t)i;
+    }
+    int err = 0;
+    if (nch == 1) {
+        pl->n = 0;
+        err = pairs_of_cells(pos, L, G, head, next, rcut, 0, nc, pl);
+    } else {
+#pragma omp parallel for schedule(static, 1) reduction(| : err)
+        for (int k = 0; k < nch; k++)
+            err |= pairs_of_cells(pos, L, G, head, next, rcut, nc * k / nch, nc * (k + 1) / nch, &part[k]);
+        int64_t total = 0;
+        for (int k = 0; k < nch; k++) total += part[k].n;
+        if (!err && total > pl->cap) {
+            pair_t* q = (pair_t*)realloc(pl->p, (size_t)(total > 0 ? total : 1) * sizeof(pair_t));
+            if (q) { pl->p = q; pl->cap = total; }
+            else err = 1;
+        }
+        pl->n = 0;
+        for (int k = 0; k < nch && !err; k++) {
+            if (part[k].n) memcpy(pl->p + pl->n, part[k].p, (size_t)part[k].n * sizeof(pair_t));
+            pl->n += part[k].n;
+        }
+        for (int k = 0; k < nch; k++) free(part[k].p);
+    }
+    free(head); free(next); free(cell); free(part);
+    return err ? -1 : 0;
 }
 
 static void emit_pairs(const pairlist_t* pl, int64_t cap, int32_t* out)
@@ -277,16 +336,15 @@ double orc_pair_r2(const double* pos, const double L[3], int64_t i, int64_t j)
 /* Forces, energy, virial                                              */
 /* ------------------------------------------------------------------ */
 
-/* Pair-list force evaluation with Newton's third law (Sec. 3.2): each listed
- * pair within rc adds fr * r to atom i and subtracts it from atom j.
- * U = sum u(r); W = sum r . f over pairs. */
-static void forces_from_pairs(int64_t n, const double* pos, const double L[3], const pairlist_t* pl,
-                              double rc, double ushift, double* f, double* pe, double* vir)
+/* The pairs [m_beg, m_end) of a pair list: each pair within rc adds fr * r
+ * to atom i and subtracts it from atom j in f (Newton's third law,
+ * Sec. 3.2); U and W, the sums of u(r) and r . f, are added to *pe, *vir. */
+static void forces_of_pairs(const double* pos, const double L[3], const pairlist_t* pl, int64_t m_beg,
+                            int64_t m_end, double rc, double ushift, double* f, double* pe, double* vir)
 {
     double rc2 = rc * rc;
     double U = 0.0, W = 0.0;
-    memset(f, 0, (size_t)n * 3 * sizeof(double));
-    for (int64_t m = 0; m < pl->n; m++) {
+    for (int64_t m = m_beg; m < m_end; m++) {
         const pair_t* e = &pl->p[m];
         double dx = pos[3 * e->i + 0] - pos[3 * e->j + 0] + e->s[0] * L[0];
         double dy = pos[3 * e->i + 1] - pos[3 * e->j + 1] + e->s[1] * L[1];
@@ -309,6 +367,47 @@ static void forces_from_pairs(int64_t n, const double* pos, const double L[3], c
     *vir = W;
 }
 
+/* Force arrays of the chunks k > 0 (none with a single chunk). */
+static double* chunk_forces_alloc(int64_t n)
+{
+    int nch = n_chunks();
+    if (nch == 1) return NULL;
+    return (double*)malloc((size_t)(nch - 1) * (size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
+}
+
+/* Pair-list force evaluation (forces_of_pairs over the whole list).  With
+ * several chunks, chunk k > 0 sums into its own array of fk, and the arrays
+ * and the chunk sums are added in chunk order afterwards. */
+static void forces_from_pairs(int64_t n, const double* pos, const double L[3], const pairlist_t* pl,
+                              double rc, double ushift, double* f, double* fk, double* pe, double* vir)
+{
+    int nch = n_chunks();
+    if (nch == 1 || !fk) {
+        memset(f, 0, (size_t)n * 3 * sizeof(double));
+        forces_of_pairs(pos, L, pl, 0, pl->n, rc, ushift, f, pe, vir);
+        return;
+    }
+    double sums[2 * 1024];
+    if (nch > 1024) nch = 1024;
+#pragma omp parallel for schedule(static, 1)
+    for (int k = 0; k < nch; k++) {
+        double* fo = k == 0 ? f : fk + (size_t)(k - 1) * (size_t)n * 3;
+        memset(fo, 0, (size_t)n * 3 * sizeof(double));
+        forces_of_pairs(pos, L, pl, pl->n * k / nch, pl->n * (k + 1) / nch, rc, ushift, fo,
+                        &sums[2 * k], &sums[2 * k + 1]);
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < 3 * n; q++)
+        for (int k = 1; k < nch; k++) f[q] += fk[(size_t)(k - 1) * (size_t)n * 3 + q];
+    double U = 0.0, W = 0.0;
+    for (int k = 0; k < nch; k++) {
+        U += sums[2 * k];
+        W += sums[2 * k + 1];
+    }
+    *pe = U;
+    *vir = W;
+}
+
 /* Forces through the cell lists (pairs within rc, no skin).  Returns 0 or -1. */
 int orc_forces_cells(int64_t n, const double* pos, const double L[3], const int G[3], double rc,
                      double ushift, double* f, double* pe, double* vir)
@@ -316,7 +415,9 @@ int orc_forces_cells(int64_t n, const double* pos, const double L[3], const int 
     if (G[0] < 3 || G[1] < 3 || G[2] < 3) return -1;
     pairlist_t pl = {0, 0, 0};
     if (build_pairs_cells(n, pos, L, G, rc, &pl)) { free(pl.p); return -1; }
-    forces_from_pairs(n, pos, L, &pl, rc, ushift, f, pe, vir);
+    double* fk = chunk_forces_alloc(n);
+    forces_from_pairs(n, pos, L, &pl, rc, ushift, f, fk, pe, vir);
+    free(fk);
     free(pl.p);
     return 0;
 }
@@ -436,46 +537,51 @@ int orc_run(int64_t n, double* pos, double* vel, const orc_params_t* P, int64_t 
     if (orc_cell_grid(P->L, rn, P->even_cells, G)) return -1;
     double* f = (double*)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
     double* xb = (double*)malloc((size_t)(n > 0 ? n : 1) * 3 * sizeof(double));
-    if (!f || !xb) { free(f); free(xb); return -2; }
+    double* fk = chunk_forces_alloc(n);
+    if (!f || !xb || (n_chunks() > 1 && !fk)) { free(f); free(xb); free(fk); return -2; }
     pairlist_t pl = {0, 0, 0};
     double h = 0.5 * P->dt;
     double half_skin2 = 0.25 * P->skin * P->skin;
     int64_t nreb = 0, psum = 0;
 
     orc_wrap(n, pos, P->L);
-    if (build_pairs_cells(n, pos, P->L, G, rn, &pl)) { free(f); free(xb); free(pl.p); return -2; }
+    if (build_pairs_cells(n, pos, P->L, G, rn, &pl)) { free(f); free(xb); free(fk); free(pl.p); return -2; }
     psum += pl.n;
     memcpy(xb, pos, (size_t)n * 3 * sizeof(double));
     double U, W;
-    forces_from_pairs(n, pos, P->L, &pl, P->rc, P->ushift, f, &U, &W);
+    forces_from_pairs(n, pos, P->L, &pl, P->rc, P->ushift, f, fk, &U, &W);
     if (ke) ke[0] = kinetic(n, vel);
     if (pe) pe[0] = U;
     if (vir) vir[0] = W;
 
     for (int64_t step = 1; step <= nsteps; step++) {
         /* (a) half kick, drift */
+#pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < 3 * n; k++) {
             vel[k] = vel[k] + h * f[k];
             pos[k] = pos[k] + P->dt * vel[k];
         }
         /* (b) rebuild when the largest displacement reaches skin/2 */
-        int rebuild = (P->skin == 0.0);
-        for (int64_t i = 0; i < n && !rebuild; i++) {
+        int far = 0;
+#pragma omp parallel for schedule(static) reduction(| : far)
+        for (int64_t i = 0; i < n; i++) {
             double dx = pos[3 * i + 0] - xb[3 * i + 0];
             double dy = pos[3 * i + 1] - xb[3 * i + 1];
             double dz = pos[3 * i + 2] - xb[3 * i + 2];
-            if (dx * dx + dy * dy + dz * dz >= half_skin2) rebuild = 1;
+            if (dx * dx + dy * dy + dz * dz >= half_skin2) far = 1;
         }
+        int rebuild = (P->skin == 0.0) || far;
         if (rebuild) {
             orc_wrap(n, pos, P->L);
-            if (build_pairs_cells(n, pos, P->L, G, rn, &pl)) { free(f); free(xb); free(pl.p); return -2; }
+            if (build_pairs_cells(n, pos, P->L, G, rn, &pl)) { free(f); free(xb); free(fk); free(pl.p); return -2; }
             psum += pl.n;
             memcpy(xb, pos, (size_t)n * 3 * sizeof(double));
             nreb++;
         }
         /* (c) forces */
-        forces_from_pairs(n, pos, P->L, &pl, P->rc, P->ushift, f, &U, &W);
+        forces_from_pairs(n, pos, P->L, &pl, P->rc, P->ushift, f, fk, &U, &W);
         /* (d) half kick */
+#pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < 3 * n; k++) vel[k] = vel[k] + h * f[k];
         /* (e) properties */
         if (ke) ke[step] = kinetic(n, vel);
@@ -494,6 +600,6 @@ int orc_run(int64_t n, double* pos, double* vel, const orc_params_t* P, int64_t 
     if (f_out) memcpy(f_out, f, (size_t)n * 3 * sizeof(double));
     if (nrebuild) *nrebuild = nreb;
     if (npairs_sum) *npairs_sum = psum;
-    free(f); free(xb); free(pl.p);
+    free(f); free(xb); free(fk); free(pl.p);
     return 0;
 }
