@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--serve-low-rate", type=float, default=10.0,
                     help="arrival rate of the second, below-saturation trace")
     ap.add_argument("--eager", action="store_true", help="stream launches instead of graphs")
+    ap.add_argument("--build", default="auto", choices=["auto", "thread", "warp"],
+                    help="neighbour-list build kernel (md_params.build_kernel)")
     ap.add_argument("--profile-steps", type=int, default=2,
                     help="benchmark steps run with per-kernel CUDA events for the roofline")
     return ap.parse_args()
@@ -399,7 +401,7 @@ def run_ours(args):
 
     def make(precision):
         s = md.Simulation(L, n, cfg.get("rc", RC), cfg["skin"], DT, precision=precision, reorder_interval=100,
-                          use_graphs=not args.eager, stream=stream.cuda_stream, device=local)
+                          use_graphs=not args.eager, stream=stream.cuda_stream, device=local, build=args.build)
         s.set_state(pos, vel)
         return s
 

@@ -93,8 +93,23 @@ typedef struct md_params {
                                  potential of Sec. 3.1), else 0.               */
     void* stream;             /* cudaStream_t to run on; NULL (default) = a
                                  stream created and owned by the handle.       */
-    int64_t reserved[6];
+    int32_t build_kernel;     /* neighbour-list build (Sec. 3.4): MD_BUILD_AUTO
+                                 (default, = MD_BUILD_THREAD), MD_BUILD_THREAD
+                                 (one thread per atom scans its 27 cells) or
+                                 MD_BUILD_WARP (warp-cooperative: one warp per
+                                 home cell gathers the 27 cells' candidates
+                                 once, its lanes test them against one home
+                                 atom at a time).  The lists hold the same
+                                 pairs; in the mixed form the trajectories
+                                 are the same bits.                           */
+    int32_t reserved32;
+    int64_t reserved[5];
 } md_params;
+
+#define MD_BUILD_AUTO   0  /* the faster build on the workloads measured:
+                              MD_BUILD_THREAD                                 */
+#define MD_BUILD_THREAD 1
+#define MD_BUILD_WARP   2
 
 /* Geometry and resource plan, computed on the host without a GPU. */
 typedef struct md_plan_t {

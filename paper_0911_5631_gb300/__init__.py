@@ -35,6 +35,11 @@ MD_ENODEV = -7
 MD_PREC_MIXED = 0
 MD_PREC_FP64 = 1
 
+MD_BUILD_AUTO = 0
+MD_BUILD_THREAD = 1
+MD_BUILD_WARP = 2
+_BUILD = {"auto": MD_BUILD_AUTO, "thread": MD_BUILD_THREAD, "warp": MD_BUILD_WARP}
+
 WCA_RC = 2.0 ** (1.0 / 6.0)
 
 
@@ -60,7 +65,9 @@ class md_params(C.Structure):
         ("shell_bins", C.c_int32),
         ("ushift", C.c_double),
         ("stream", C.c_void_p),
-        ("reserved", C.c_int64 * 6),
+        ("build_kernel", C.c_int32),
+        ("reserved32", C.c_int32),
+        ("reserved", C.c_int64 * 5),
     ]
 
 
@@ -368,9 +375,10 @@ class Simulation:
 
     def __init__(self, box, n, rc=WCA_RC, skin=0.4, dt=0.005, precision="mixed", reorder_interval=100,
                  cell_list_only=False, even_cells=False, nbr_capacity=0, use_graphs=True, ushift=None,
-                 stream=None, device=-1, shell_bins=True):
+                 stream=None, device=-1, shell_bins=True, build="auto"):
         p = md_default_params()
         p.shell_bins = int(bool(shell_bins))
+        p.build_kernel = _BUILD[build] if isinstance(build, str) else int(build)
         p.precision = MD_PREC_FP64 if precision in ("fp64", MD_PREC_FP64) else MD_PREC_MIXED
         p.reorder_interval = int(reorder_interval)
         p.cell_list_only = int(bool(cell_list_only))

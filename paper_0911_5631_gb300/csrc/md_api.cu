@@ -237,6 +237,13 @@ struct Sim : SimBase {
         return (unsigned)((m + kBlock - 1) / kBlock);
     }
 
+    // the neighbour-list build: a block of kWcThreads per x slice of a
+    // pencil (a warp per cell), or a thread per cell-ordered atom
+    bool warp_build() const { return use_warp_build(prm); }
+    void* build_fn() const { return warp_build() ? kt.build_wc : kt.build; }
+    unsigned grid_build() const { return warp_build() ? (unsigned)wc_slices(a) : grid_atoms(); }
+    unsigned block_build() const { return warp_build() ? (unsigned)kWcThreads : (unsigned)kBlock; }
+
     void* step_fn(bool final_node) const {
         if (prm.cell_list_only) return final_node ? kt.step_cells_final : kt.step_cells;
         return final_node ? kt.step_list_final : kt.step_list;
@@ -253,7 +260,7 @@ struct Sim : SimBase {
         MD_CUDA(launch(kt.cellsort, grid_cells(), kBlock, a, g));
         MD_CUDA(launch(kt.gather, grid_atoms(), kBlock, a, g));
         MD_CUDA(launch(kt.commit, grid_atoms(), kBlock, a, g));
-        if (!prm.cell_list_only) MD_CUDA(launch(kt.build, grid_atoms(), kBlock, a, g));
+        if (!prm.cell_list_only) MD_CUDA(launch(build_fn(), grid_build(), block_build(), a, g));
         MD_CUDA(launch(kt.rebuild_done, 1, 32, a, g));
         return MD_OK;
     }
@@ -309,7 +316,7 @@ struct Sim : SimBase {
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.gather, grid_atoms(), kBlock, a, g)));
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.commit, grid_atoms(), kBlock, a, g)));
         if (!prm.cell_list_only)
-            MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.build, grid_atoms(), kBlock, a, g)));
+            MD_CUDA(chain(add_kernel(body, &prev, &cur, build_fn(), grid_build(), block_build(), a, g)));
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.rebuild_done, 1, 32, a, g)));
         return MD_OK;
     }

@@ -129,6 +129,8 @@ struct alignas(16) Args {
     double w[3];        // cell widths
     double hw[3];       // half cell widths
     float hwf_in[3];    // FP32 bound below which an offset is surely inside its cell
+    float pad1;
+    double hw_in[3];    // FP64 bound below which the whole-cell moves of a re-binning are exact
     float wf[3];
     double dt, h;       // time step and half step
     float dtf, hf;
@@ -184,5 +186,13 @@ struct alignas(16) Args {
     double* io_pos;     // [3 n] staging for set/get (user order, AoS)
     double* io_vel;     // [3 n]
 };
+
+// x slices of the pencil cell order (tiles of 4 x 4 cells in (y, z), each
+// taken at every c_x): the thread blocks of the warp-cooperative build.
+constexpr int kWcThreads = 512;  // one warp per cell of a slice
+template <class P>
+__host__ __device__ __forceinline__ int64_t wc_slices(const Args<P>& a) {
+    return (int64_t)((a.G[1] + 3) / 4) * ((a.G[2] + 3) / 4) * a.G[0];
+}
 
 }  // namespace md

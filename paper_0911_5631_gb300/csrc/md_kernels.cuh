@@ -775,11 +775,11 @@ __global__ void k_clear_overflow(Counters* C) {
 // ---------------------------------------------------------------------------
 
 // Re-anchors every atom at its current position: the FP64 offset pb + o
-// becomes the new build offset (o restarts from the rounding remainder).  An
-// atom whose offset is not clearly inside its cell is binned afresh by the
-// cell rule above, from the position md_get_state reports (periodic wrap
-// included), and takes its offset from the new cell's centre.  Refreshes the
-// pair coordinate and counts the atoms of each cell.
+// becomes the new build offset (o restarts from the rounding remainder), and
+// an atom whose offset left its cell moves to the cell the rule above gives
+// for the position md_get_state reports (periodic wrap is an integer
+// operation on the cell coordinate).  Refreshes the pair coordinate and
+// counts the atoms of each cell.
 template <class P>
 __device__ __forceinline__ void bin_item(const Args<P>& a, int64_t i) {
     using real = typename P::real;
@@ -794,11 +794,23 @@ __device__ __forceinline__ void bin_item(const Args<P>& a, int64_t i) {
     for (int d = 0; d < 3; d++) {
         const double t = full_offset(pbp[d][i], op[d][i]);
         split_offset(t, pb[d], o[d]);
-        // an offset clearly inside the cell keeps it (the rule gives the same
-        // cell with a margin of 1e-6 w); NaN fails the test
+        // An offset clearly inside the cell keeps it (the rule gives the same
+        // cell with a margin of 1e-6 w); NaN fails the test.  Otherwise the
+        // atom moves by whole cells while its offset lies outside
+        // [-w/2, w/2), which is what the rule decides as long as the new
+        // offset stays 1e-9 w/2 or more inside the faces (the rounding of the
+        // rule is below 1e-13 w for any region of up to 10^5 cells); an
+        // offset closer to a face, or an atom more than two cells away, is
+        // binned by the rule itself from the reported position.
         if (!(fabsf(to_f32(pb[d])) < a.hwf_in[d])) {
-            double tn;
-            bad |= !bin_coord(a, d, abs_coord(a, d, cc[d], t), cc[d], tn);
+            double tn = t;
+            int c = cc[d];
+            for (int it = 0; it < 2; it++) {
+                if (tn >= a.hw[d]) { tn = __dsub_rn(tn, a.w[d]); c = wrap_add(c, 1, a.G[d]); }
+                else if (tn < -a.hw[d]) { tn = __dadd_rn(tn, a.w[d]); c = wrap_add(c, -1, a.G[d]); }
+            }
+            if (!(fabs(tn) < a.hw_in[d])) bad |= !bin_coord(a, d, abs_coord(a, d, cc[d], t), c, tn);
+            cc[d] = c;
             split_offset(tn, pb[d], o[d]);
         }
         pbp[d][i] = pb[d];
@@ -1038,29 +1050,37 @@ __global__ void __launch_bounds__(kBlock) k_commit(Args<P> a, int guard) {
     commit_item<P>(a, s);
 }
 
-// Exact FP64 neighbour criterion r^2 < r_n^2 for atom i in cell ci and atom
-// j in the stencil cell ci + d, evaluated as the FP64 reference evaluates
-// its cell pairs (Sec. 3.2): e = (x_i - x_j) + s L on the reported absolute
-// coordinates, s = -1 / +1 when ci + d wraps across the upper / lower face,
+// Exact FP64 neighbour criterion r^2 < r_n^2 for atom i and atom j, whose
+// cell lies at offset d from i's cell (code = (d_x+1) | (d_y+1) << 2 |
+// (d_z+1) << 4), evaluated as the FP64 reference evaluates its cell pairs
+// (Sec. 3.2): e = (x_i - x_j) + s L on the reported absolute coordinates,
+// s = -1 / +1 when i's cell + d wraps across the upper / lower face,
 // r^2 = (e_x^2 + e_y^2) + e_z^2, every operation rounded, no contraction.
+// The reported coordinate k of atom i when its cell coordinate is c.
 template <class P>
-__device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, int cx, int cy, int cz, int dx, int dy,
-                                            int dz) {
-    const int ci[3] = {cx, cy, cz}, dd[3] = {dx, dy, dz};
-    const typename P::real* pb[3] = {a.pbx, a.pby, a.pbz};
-    const double* o[3] = {a.ox, a.oy, a.oz};
-    double e[3];
-#pragma unroll
+__device__ __noinline__ double reported_coord(const Args<P>& a, int k, int c, int i) {
+    const typename P::real* pb = k == 0 ? a.pbx : (k == 1 ? a.pby : a.pbz);
+    const double* o = k == 0 ? a.ox : (k == 1 ? a.oy : a.oz);
+    return abs_coord(a, k, c, full_offset(pb[i], o[i]));
+}
+
+template <class P>
+__device__ __noinline__ bool within_rn_fp64(const Args<P>& a, int i, int j, unsigned code) {
+    int ci[3];
+    unpack_cell(a.cell[i], ci[0], ci[1], ci[2]);
+    double r2 = 0.0;
+#pragma unroll 1
     for (int k = 0; k < 3; k++) {
-        int cj = ci[k] + dd[k];
+        int cj = ci[k] + (int)((code >> (2 * k)) & 3u) - 1;
         double s = 0.0;
         if (cj >= a.G[k]) { cj -= a.G[k]; s = -1.0; }
         else if (cj < 0) { cj += a.G[k]; s = 1.0; }
-        const double xi = abs_coord(a, k, ci[k], full_offset(pb[k][i], o[k][i]));
-        const double xj = abs_coord(a, k, cj, full_offset(pb[k][j], o[k][j]));
-        e[k] = __dadd_rn(__dsub_rn(xi, xj), __dmul_rn(s, a.L[k]));
+        const double xi = reported_coord(a, k, ci[k], i);
+        const double xj = reported_coord(a, k, cj, j);
+        const double e = __dadd_rn(__dsub_rn(xi, xj), __dmul_rn(s, a.L[k]));
+        // (e_x^2 + e_y^2) + e_z^2: the first product is added to an exact 0
+        r2 = __dadd_rn(r2, __dmul_rn(e, e));
     }
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(e[0], e[0]), __dmul_rn(e[1], e[1])), __dmul_rn(e[2], e[2]));
     return r2 < a.rn2;
 }
 
@@ -1089,7 +1109,8 @@ __device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
 // the 27 cells around its cell and record every j != i with r < r_n in its
 // column together with the cell-offset code.  The decision is the exact
 // FP64 criterion: FP32 coordinates settle every candidate outside a narrow
-// band around r_n^2, the FP64 test the rest.  The three cells of one
+// band around r_n^2, the FP64 test the rest (in build_band, after the scan,
+// so that the rare FP64 path costs the scan loop no registers).  The three cells of one
 // (c_y, c_z) row sit at base + c_x * stride in the pencil order, so each row
 // costs one index computation and the six range bounds are read together.
 //
@@ -1101,10 +1122,48 @@ __device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
 // counts sit in the bytes of one 64-bit word) and lim receives the number
 // of entries below each bin boundary.  An atom with more entries keeps its
 // order of discovery and a lim of "all entries".
+// The candidates of the atom in cell-ordered slot s whose FP32 distance lies
+// in the band around r_n^2, decided by the exact FP64 criterion and
+// appended to its list after the m entries already there (they belong to
+// the last shell bin).  A second pass over the 27 cells, run only for an
+// atom that met such a candidate.  Returns the new count.
+template <class P, bool kSort>
+__device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2* stage, int stride) {
+    const float4 ci = a.cand[s];
+    const int i = __float_as_int(ci.w);
+    int cx, cy, cz;
+    unpack_cell(a.cell[i], cx, cy, cz);
+    int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
+    const int cap = a.cap, n = (int)a.n;
+    for (int d = 0; d < 27; d++) {
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const int c = cell_index(wrap_add(cx, dx, a.G[0]), wrap_add(cy, dy, a.G[1]), wrap_add(cz, dz, a.G[2]), a.G);
+        const int end = min(a.cell_start[c + 1], n);
+        const unsigned code = (unsigned)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4));
+        for (int t = a.cell_start[c]; t < end; t++) {
+            if (t == (int)s) continue;
+            const float4 pj = __ldg(a.cand + t);
+            const float ex = (ci.x - (float)dx * a.wf[0]) - pj.x;
+            const float ey = (ci.y - (float)dy * a.wf[1]) - pj.y;
+            const float ez = (ci.z - (float)dz * a.wf[2]) - pj.z;
+            const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (!(rr >= a.rn2_lo && rr < a.rn2_hi)) continue;
+            const int j = __float_as_int(pj.w);
+            if (!within_rn_fp64(a, i, j, code)) continue;
+            const int e = j | (int)(code << kCodeShift);
+            if (kSort && m < kBuildStage) stage[m * stride] = make_int2(e, __float_as_int(rr));
+            else if (m < cap) col[(size_t)m * 32] = e;
+            m++;
+        }
+    }
+    return m;
+}
+
 template <class P, bool kSort>
 __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* stage, int stride) {
     Counters* C = a.ctr;
     int m = 0;
+    bool unsure = false;  // a candidate in the band around r_n^2 was met
     const float4 ci = a.cand[s];
     const int i = __float_as_int(ci.w);
     int cx, cy, cz;
@@ -1140,9 +1199,8 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
                     const float ez = qz - pj.z;
                     const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
                     const int j = __float_as_int(pj.w);
-                    bool take = rr < lo2;
-                    if (!take && rr < hi2) take = within_rn_fp64(a, i, j, cx, cy, cz, k - 1, dy, dz);
-                    take = take && t != self;
+                    bool take = rr < lo2 && t != self;
+                    unsure |= !(rr < lo2) && rr < hi2 && t != self;
                     if constexpr (kSort) {
                         if (take && m < kBuildStage) stage[m * stride] = make_int2(j | code, __float_as_int(rr));
                         if (take && m >= kBuildStage && m < cap) col[(size_t)m * 32] = j | code;
@@ -1154,6 +1212,7 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
             }
         }
     }
+    if (unsure) m = build_band<P, kSort>(a, s, m, stage, stride);
     const int kept = m < cap ? m : cap;
     a.nn[i] = kept;
     unsigned long long incl = ~0ull;  // lim byte 255: read all entries
@@ -1214,6 +1273,209 @@ __global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
     int bm = block_max_int(m, shm);
     double bs = block_sum((double)m, shs);
     if (threadIdx.x == 0) {
+        atomicMax(&C->max_nn, bm);
+        atomicAdd((unsigned long long*)&C->list_entries, (unsigned long long)bs);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp-cooperative neighbour-list build (Sec. 3.4, W_{m,i} and m_i)
+// ---------------------------------------------------------------------------
+//
+// One thread block per x slice of a pencil (the up to 4 x 4 cells of one
+// tile at one c_x, consecutive in the cell order) and one warp per cell of
+// the slice.  The warp gathers the candidates of the 27 cells around its
+// home cell into shared memory once -- each shifted into the home cell's
+// frame (x_j + d w) and tagged with its entry j | code << kCodeShift -- and
+// then takes the home atoms one at a time: every lane tests one candidate,
+// so the warp has no per-lane loops of uneven length and every candidate is
+// loaded once per home cell instead of once per home atom.  The decision is
+// the one of the thread-per-atom build (FP32 outside a narrow band around
+// r_n^2, the exact FP64 criterion inside it).  Accepted entries are
+// compacted by ballot into a per-warp stage; a list of at most kWcSort
+// entries is then written ordered by shell bin, each lane placing one entry
+// at (entries of lower bins) + (entries of its bin before it), both counted
+// from three ballots over the bits of the bin, and lim receives the counts
+// below each bin boundary.  A longer list keeps its order of discovery and a
+// lim of "all entries".
+constexpr int kWcBatch = 192;   // candidates staged per warp at a time
+constexpr int kWcSort = 32;     // lists up to this long are sorted by shell bin
+constexpr int kWcWarps = kWcThreads / 32;  // one per cell of a slice
+
+struct WcWarp {
+    float4 cand[kWcBatch];
+    int2 stage[kWcSort];
+};
+
+// Cell-offset code (d_x+1) | (d_y+1) << 2 | (d_z+1) << 4 of stencil cell
+// c = (d_x+1) + 3 (d_y+1) + 9 (d_z+1).
+__device__ __forceinline__ unsigned c9_code(int c) {
+    const unsigned x = (unsigned)(c % 3), y = (unsigned)((c / 3) % 3), z = (unsigned)(c / 9);
+    return x | (y << 2) | (z << 4);
+}
+
+// Lanes (of the valid mask V, bins b held as the bit masks M0, M1, M2) whose
+// bin is below t.
+__device__ __forceinline__ unsigned bins_below(int t, unsigned V, unsigned M0, unsigned M1, unsigned M2) {
+    const unsigned E2 = (t & 4) ? M2 : ~M2, E1 = (t & 2) ? M1 : ~M1;
+    const unsigned lt2 = (t & 4) ? (V & ~M2) : 0u;
+    const unsigned lt1 = (t & 2) ? (V & E2 & ~M1) : 0u;
+    const unsigned lt0 = (t & 1) ? (V & E2 & E1 & ~M0) : 0u;
+    return lt2 | lt1 | lt0;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kWcThreads, 2) k_build_wc(Args<P> a, int guard) {
+    __shared__ WcWarp s_wc[kWcWarps];
+    __shared__ int s_max[kWcWarps];
+    __shared__ long long s_sum[kWcWarps];
+    Counters* C = a.ctr;
+    if (guard && !C->rebuild_flag) return;
+    constexpr unsigned kFull = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    WcWarp& W = s_wc[wid];
+    const int n = (int)a.n, cap = a.cap;
+    const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
+    // the slice of this block and the home cell of this warp
+    const int nty = (a.G[1] + 3) / 4;
+    const int cx = (int)(blockIdx.x % (unsigned)a.G[0]);
+    const int tile = (int)(blockIdx.x / (unsigned)a.G[0]);
+    const int y0 = (tile % nty) * 4, z0 = (tile / nty) * 4;
+    const int hy = min(4, a.G[1] - y0), hz = min(4, a.G[2] - z0);
+    int mx = 0;
+    long long sum = 0;
+    if (wid < hy * hz) {
+        const int cy = y0 + wid % hy, cz = z0 + wid / hy;
+        // this lane's stencil cell (lanes 0..26), d = (dx, dy, dz)
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+        int start = 0, cnt = 0;
+        if (lane < 27) {
+            const int c2 = cell_index(wrap_add(cx, dx, a.G[0]), wrap_add(cy, dy, a.G[1]), wrap_add(cz, dz, a.G[2]), a.G);
+            start = a.cell_start[c2];
+            cnt = max(min(a.cell_start[c2 + 1], n) - start, 0);
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int excl = incl - cnt;
+        const int K = __shfl_sync(kFull, incl, 31);
+        const int nh = __shfl_sync(kFull, cnt, 13);  // lane 13: the home cell itself
+        const int h0 = __shfl_sync(kFull, excl, 13);
+        const int hs = __shfl_sync(kFull, start, 13);
+        for (int h = 0; h < nh; h++) {
+            // the home atoms are the staged candidates of lane 13's cell (no
+            // shift) as long as they lie in the first batch
+            const bool staged_home = h0 + h < kWcBatch;
+            float4 qi;
+            if (!staged_home) qi = a.cand[hs + h];
+            const int kself = h0 + h;
+            int m = 0;
+            int i = -1;
+            int* col = nullptr;
+            for (int b0 = 0; b0 < K; b0 += kWcBatch) {
+                if (h == 0 || K > kWcBatch) {  // (re)fill the staged candidates
+                    // lanes over candidates: candidate k lies in the stencil
+                    // cell c = number of cells whose inclusive count is <= k
+                    // (binary search over the scan), slot start_c + k - excl_c
+                    __syncwarp();
+                    const int kend = min(K - b0, kWcBatch);
+#pragma unroll 2
+                    for (int r = 0; r < kend; r += 32) {
+                        const int kl = r + lane, k = b0 + kl;
+                        int c = 0;
+#pragma unroll
+                        for (int st = 16; st > 0; st >>= 1)
+                            if (__shfl_sync(kFull, incl, c + st - 1) <= k) c += st;
+                        const int sc = __shfl_sync(kFull, start, c), ec = __shfl_sync(kFull, excl, c);
+                        if (kl < kend) {
+                            const int ddx = c % 3 - 1, ddy = (c / 3) % 3 - 1, ddz = c / 9 - 1;
+                            const float4 pj = __ldg(a.cand + sc + (k - ec));
+                            W.cand[kl] = make_float4(
+                                fmaf((float)ddx, a.wf[0], pj.x), fmaf((float)ddy, a.wf[1], pj.y),
+                                fmaf((float)ddz, a.wf[2], pj.z),
+                                __int_as_float(__float_as_int(pj.w) | (int)((unsigned)c9_code(c) << kCodeShift)));
+                        }
+                    }
+                    __syncwarp();
+                }
+                if (b0 == 0) {
+                    if (staged_home) qi = W.cand[kself];
+                    i = __float_as_int(qi.w) & kIndexMask;
+                    col = a.nbr + ((size_t)(i >> 5) * (size_t)cap) * 32 + (i & 31);
+                }
+                const int kend = min(K - b0, kWcBatch);
+                for (int r = 0; r < kend; r += 32) {
+                    const int kl = r + lane;
+                    bool take = false, unsure = false;
+                    int e = 0;
+                    float rr = 0.0f;
+                    if (kl < kend && b0 + kl != kself) {
+                        const float4 c = W.cand[kl];
+                        const float ex = qi.x - c.x, ey = qi.y - c.y, ez = qi.z - c.z;
+                        rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                        e = __float_as_int(c.w);
+                        take = rr < lo2;
+                        unsure = !take && rr < hi2;
+                    }
+                    if (unsure) take = within_rn_fp64(a, i, e & kIndexMask, (unsigned)e >> kCodeShift);
+                    const unsigned bal = __ballot_sync(kFull, take);
+                    const int dst = m + __popc(bal & lt);
+                    if (take) {
+                        if (dst < kWcSort) W.stage[dst] = make_int2(e, __float_as_int(rr));
+                        else if (dst < cap) col[(size_t)dst * 32] = e;
+                    }
+                    m += __popc(bal);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) a.nn[i] = min(m, cap);
+            if (a.shell_bins && m <= kWcSort && m <= cap) {
+                const bool v = lane < m;
+                int b = 0, e = 0;
+                if (v) {
+                    const int2 st = W.stage[lane];
+                    e = st.x;
+                    b = shell_bin(a, __int_as_float(st.y));
+                }
+                const unsigned V = __ballot_sync(kFull, v);
+                const unsigned M0 = __ballot_sync(kFull, (b & 1) != 0), M1 = __ballot_sync(kFull, (b & 2) != 0),
+                               M2 = __ballot_sync(kFull, (b & 4) != 0);
+                if (v) {
+                    const unsigned same = V & ((b & 4) ? M2 : ~M2) & ((b & 2) ? M1 : ~M1) & ((b & 1) ? M0 : ~M0);
+                    col[(size_t)(__popc(bins_below(b, V, M0, M1, M2)) + __popc(same & lt)) * 32] = e;
+                }
+                if (lane >= 1 && lane < kShellBins)
+                    a.lim[(size_t)(lane - 1) * a.n + i] = (unsigned char)__popc(bins_below(lane, V, M0, M1, M2));
+            } else {
+                const int ns = min(min(m, kWcSort), cap);
+                if (lane < ns) col[(size_t)lane * 32] = W.stage[lane].x;
+                if (a.shell_bins && lane >= 1 && lane < kShellBins) a.lim[(size_t)(lane - 1) * a.n + i] = 0xff;
+            }
+            if (m > cap && lane == 0) {
+                atomicOr(&C->error, kErrOverflow);
+                atomicMax(&C->need_cap, m);
+            }
+            mx = max(mx, m);
+            sum += m;
+            __syncwarp();  // the stage is reused by the next home atom
+        }
+    }
+    if (lane == 0) {
+        s_max[wid] = mx;
+        s_sum[wid] = sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int bm = 0;
+        long long bs = 0;
+        for (int w = 0; w < kWcWarps; w++) {
+            bm = max(bm, s_max[w]);
+            bs += s_sum[w];
+        }
         atomicMax(&C->max_nn, bm);
         atomicAdd((unsigned long long*)&C->list_entries, (unsigned long long)bs);
     }
@@ -2117,6 +2379,7 @@ KernelTable<P> make_kernel_table() {
     t.gather = (void*)k_gather<P>;
     t.commit = (void*)k_commit<P>;
     t.build = (void*)k_build<P>;
+    t.build_wc = (void*)k_build_wc<P>;
     t.rebuild_done = (void*)k_rebuild_done<P>;
     t.cond = (void*)k_cond<P>;
     t.kickdrift = (void*)k_kickdrift<P>;

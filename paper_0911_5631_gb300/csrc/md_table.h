@@ -16,7 +16,8 @@ struct KernelTable {
     void* cellsort;
     void* gather;
     void* commit;
-    void* build;
+    void* build;     // thread per atom
+    void* build_wc;  // warp per home cell (warp-cooperative)
     void* rebuild_done;
     void* cond;
     void* kickdrift;

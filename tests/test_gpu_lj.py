@@ -27,12 +27,16 @@ def _sim(pos, vel, L, rc, prec, **kw):
     return s
 
 
+@pytest.mark.parametrize("build", ["auto", "warp"])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("rc", [2.2, 2.5, 3.0])
-def test_lj_forces_pairs_energy(rc, prec):
+def test_lj_forces_pairs_energy(rc, prec, build):
+    # with r_c 3 a cell's neighbourhood holds about 560 atoms: the automatic
+    # choice is the thread-per-atom build, and the warp build stages the
+    # candidates in several batches
     n = 4000
     pos, vel, L = state(n, RHO, T, 61, jitter=0.3)
-    s = _sim(pos, vel, L, rc, prec)
+    s = _sim(pos, vel, L, rc, prec, build=build)
     pw = oracle.wrap(pos, L)
     assert s.plan()["ushift"] == 0.0  # plain truncated LJ
     f_ref, U, W = oracle.forces_cells(pw, L, oracle_grid(L, rc), rc, 0.0)

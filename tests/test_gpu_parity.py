@@ -56,12 +56,16 @@ def test_cells_bit_exact(case, prec):
     s.close()
 
 
+BUILDS = ["warp", "thread"]
+
+
+@pytest.mark.parametrize("build", BUILDS)
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_neighbor_pairs_match_oracle(case, prec):
+def test_neighbor_pairs_match_oracle(case, prec, build):
     # identical sets: the GPU decides the pairs near r_n by the reference's
     # own FP64 expression on the positions it reports
-    s, pos, vel, L, skin = _setup(case, prec)
+    s, pos, vel, L, skin = _setup(case, prec, build=build)
     p, _ = s.get_state()
     rn = RC + skin
     pairs, entries = s.neighbor_pairs()
@@ -87,15 +91,16 @@ def _check_rebuilt_state(s, L, skin, G):
     return len(pairs)
 
 
+@pytest.mark.parametrize("build", BUILDS)
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", CASES, ids=IDS)
-def test_rebuilds_along_trajectory_match_oracle(case, prec):
+def test_rebuilds_along_trajectory_match_oracle(case, prec, build):
     # The rebuilds of md_step re-bin atoms incrementally (k_bin) and rebuild
     # the lists in place, with periodic reorders; right after every step
     # that rebuilt, the stored cells and the list must be the reference's
     # for the positions of that moment.  No md_set_state in between.
     pos, vel, L, skin = _fluid(case)
-    s = sim(pos, vel, L, skin=skin, precision=prec, reorder_interval=15)
+    s = sim(pos, vel, L, skin=skin, precision=prec, reorder_interval=15, build=build)
     G = np.array(s.plan()["G"])
     seen, last, steps = 0, s.measure()["rebuilds"], 0
     while seen < 4 and steps < 400:
@@ -119,6 +124,26 @@ def test_pair_sets_identical_across_precisions(case):
     assert np.array_equal(pa[np.lexsort(pa.T[::-1])], pb[np.lexsort(pb.T[::-1])])
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("case", CASES[:4], ids=IDS[:4])
+def test_builds_give_the_same_trajectory(case):
+    # The warp-per-cell and thread-per-atom builds store each atom's entries
+    # in different orders, with the same pairs and the same shell-bin counts
+    # up to rounding; a step reads only entries that cannot interact beyond
+    # its shell reach, and the mixed form sums in integers, so the two
+    # trajectories are the same bits.
+    pos, vel, L, skin = _fluid(case)
+    out = []
+    for build in BUILDS:
+        s = sim(pos, vel, L, skin=skin, precision="mixed", reorder_interval=25, build=build)
+        s.step(120)
+        out.append(s.get_state() + (s.measure(),))
+        s.close()
+    (p0, v0, m0), (p1, v1, m1) = out
+    assert m0["rebuilds"] == m1["rebuilds"] >= 4
+    assert m0["list_entries"] == m1["list_entries"] and m0["max_neighbors"] == m1["max_neighbors"]
+    assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
 
 
 @pytest.mark.parametrize("prec", PRECS)
