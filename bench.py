@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--ens-steps", type=int, default=inputs.ENSEMBLE["steps"])
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace lines")
     ap.add_argument("--no-lj", action="store_true", help="skip the Lennard-Jones line")
-    ap.add_argument("--ablations", action="store_true", help="add the reorder-interval and shell-bin ablations")
+    ap.add_argument("--no-ablations", action="store_true",
+                    help="skip the ablations (reorder interval, shell bins, kernel variants, builds)")
     ap.add_argument("--serve-requests", type=int, default=48)
     ap.add_argument("--serve-low-rate", type=float, default=10.0,
                     help="arrival rate of the second, below-saturation trace")
@@ -345,19 +346,40 @@ def lj_bench(md, torch, stream, device, steps, chunk=100):
         s.close()
 
 
+ABLATIONS = [
+    # (label, Simulation keyword arguments): the paper's Tables 7 and 8
+    # (reorder interval; 0 = never after the load), reading every list entry
+    # at every step as the paper does (shell bins off), the texture-cache
+    # remark of Sec. 4.4 (plain loads), W transposed, Table 6 (threads per
+    # block of the force kernel), and the warp-cooperative build
+    ("reorder_0", {"reorder_interval": 0}),
+    ("reorder_20", {"reorder_interval": 20}),
+    ("reorder_100 (default)", {"reorder_interval": 100}),
+    ("reorder_500", {"reorder_interval": 500}),
+    ("shell_bins_off", {"shell_bins": False}),
+    ("plain_loads", {"variant": "plain_loads"}),
+    ("w_transposed", {"variant": "list_rows"}),
+    ("block_64", {"variant": "block64"}),
+    ("block_128", {"variant": "block128"}),
+    ("warp_build", {"build": "warp"}),
+]
+
+
 def ablations(md, torch, stream, device, pos, vel, L, cfg, chunk=100, steps=5):
-    """The paper's ablations on the 1M workload (mixed form): the reorder
-    interval (Tables 7, 8; 0 = never after the load), and lists read whole at
-    every step as in the paper (shell bins off) -- atom-steps/s, the step
-    kernel's time and the rebuild branch's time, each from an equilibrated
-    state."""
+    """The paper's ablations on the 1M workload (mixed form), each from the
+    equilibrated state: 1000 untimed steps (long enough for the storage
+    order to drift from the cell order), then `steps` x `chunk` timed MD
+    steps (graphs, CUDA events) and one profiled chunk for the step kernel's
+    and the rebuild branch's own times."""
     out = []
-    for interval, bins in ((0, True), (20, True), (100, True), (500, True), (100, False)):
-        s = md.Simulation(L, cfg["n"], cfg.get("rc", RC), cfg["skin"], DT, precision="mixed", reorder_interval=interval,
-                          stream=stream.cuda_stream, device=device, shell_bins=bins)
+    for label, kw in ABLATIONS:
+        kw = dict(kw)
+        kw.setdefault("reorder_interval", 100)
+        s = md.Simulation(L, cfg["n"], cfg.get("rc", RC), cfg["skin"], DT, precision="mixed",
+                          stream=stream.cuda_stream, device=device, **kw)
         try:
             s.set_state(pos, vel)
-            s.step(1000)  # long enough for the storage order to drift from the cell order
+            s.step(1000)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -374,7 +396,7 @@ def ablations(md, torch, stream, device, pos, vel, L, cfg, chunk=100, steps=5):
             s.set_profiling(False)
             kl = k1["step_kernel_launches"] - k0["step_kernel_launches"]
             rb = k1["rebuilds_timed"] - k0["rebuilds_timed"]
-            out.append({"reorder_interval": interval, "shell_bins": bins,
+            out.append({"ablation": label, "params": kw,
                         "value": cfg["n"] * chunk * steps / (ms / 1e3), "unit": UNIT,
                         "step_kernel_us": 1e3 * (k1["step_kernel_ms"] - k0["step_kernel_ms"]) / max(kl, 1),
                         "rebuild_us": 1e3 * (k1["rebuild_ms"] - k0["rebuild_ms"]) / rb if rb else None,
@@ -527,7 +549,7 @@ def run_ours(args):
     if rank == 0 and not args.no_ensemble:
         ens = ensemble_bench(md, torch, stream, local, args.ens_replicas, args.ens_steps, 10)
     abl = None
-    if rank == 0 and args.ablations:
+    if rank == 0 and not args.no_ablations:
         abl = ablations(md, torch, stream, local, eq_pos, eq_vel, L, cfg)
     lj = None
     if rank == 0 and not args.no_lj:

@@ -102,9 +102,26 @@ typedef struct md_params {
                                  atom at a time).  The lists hold the same
                                  pairs; in the mixed form the trajectories
                                  are the same bits.                           */
-    int32_t reserved32;
+    int32_t variant;          /* 0 (default), or one MD_VARIANT_* flag: a step
+                                 kernel variant of the paper's ablations (mixed
+                                 form with a neighbour list only).  Every
+                                 variant gives the default's trajectories, bit
+                                 for bit; only the speed differs.             */
     int64_t reserved[5];
 } md_params;
+
+/* Kernel variants of the paper's ablations (Sec. 5): */
+#define MD_VARIANT_PLAIN_LOADS 1  /* gathers of neighbour coordinates through
+                                     plain coherent loads instead of the
+                                     read-only path (the texture cache of
+                                     Sec. 4.4)                                */
+#define MD_VARIANT_LIST_ROWS   2  /* W transposed: each atom's entries
+                                     contiguous (entry m of atom i at
+                                     i * capacity + m) instead of a warp's 32
+                                     columns interleaved                      */
+#define MD_VARIANT_BLOCK64     4  /* force + integrate kernel with 64 threads
+                                     per block (Table 6; default 256)         */
+#define MD_VARIANT_BLOCK128    8  /* ... with 128 threads per block           */
 
 #define MD_BUILD_AUTO   0  /* the faster build on the workloads measured:
                               MD_BUILD_THREAD                                 */

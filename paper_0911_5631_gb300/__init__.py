@@ -40,6 +40,13 @@ MD_BUILD_THREAD = 1
 MD_BUILD_WARP = 2
 _BUILD = {"auto": MD_BUILD_AUTO, "thread": MD_BUILD_THREAD, "warp": MD_BUILD_WARP}
 
+MD_VARIANT_PLAIN_LOADS = 1
+MD_VARIANT_LIST_ROWS = 2
+MD_VARIANT_BLOCK64 = 4
+MD_VARIANT_BLOCK128 = 8
+VARIANTS = {"default": 0, "plain_loads": MD_VARIANT_PLAIN_LOADS, "list_rows": MD_VARIANT_LIST_ROWS,
+            "block64": MD_VARIANT_BLOCK64, "block128": MD_VARIANT_BLOCK128}
+
 WCA_RC = 2.0 ** (1.0 / 6.0)
 
 
@@ -66,7 +73,7 @@ class md_params(C.Structure):
         ("ushift", C.c_double),
         ("stream", C.c_void_p),
         ("build_kernel", C.c_int32),
-        ("reserved32", C.c_int32),
+        ("variant", C.c_int32),
         ("reserved", C.c_int64 * 5),
     ]
 
@@ -375,10 +382,11 @@ class Simulation:
 
     def __init__(self, box, n, rc=WCA_RC, skin=0.4, dt=0.005, precision="mixed", reorder_interval=100,
                  cell_list_only=False, even_cells=False, nbr_capacity=0, use_graphs=True, ushift=None,
-                 stream=None, device=-1, shell_bins=True, build="auto"):
+                 stream=None, device=-1, shell_bins=True, build="auto", variant="default"):
         p = md_default_params()
         p.shell_bins = int(bool(shell_bins))
         p.build_kernel = _BUILD[build] if isinstance(build, str) else int(build)
+        p.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
         p.precision = MD_PREC_FP64 if precision in ("fp64", MD_PREC_FP64) else MD_PREC_MIXED
         p.reorder_interval = int(reorder_interval)
         p.cell_list_only = int(bool(cell_list_only))

@@ -171,6 +171,7 @@ struct Sim : SimBase {
 
     void fill_scalars(int64_t n) {
         fill_args_scalars(a, plan, box, n, rc, skin, dt, prm.cell_list_only, prm.reorder_interval, prm.shell_bins);
+        a.list_rows = prm.variant == MD_VARIANT_LIST_ROWS;
     }
 
     int allocate() {
@@ -244,9 +245,32 @@ struct Sim : SimBase {
     unsigned grid_build() const { return warp_build() ? (unsigned)wc_slices(a) : grid_atoms(); }
     unsigned block_build() const { return warp_build() ? (unsigned)kWcThreads : (unsigned)kBlock; }
 
+    // index into kt.step_var of the requested ablation variant, or -1
+    int variant_index() const {
+        switch (prm.variant) {
+            case MD_VARIANT_PLAIN_LOADS: return 0;
+            case MD_VARIANT_LIST_ROWS: return 1;
+            case MD_VARIANT_BLOCK64: return 2;
+            case MD_VARIANT_BLOCK128: return 3;
+            default: return -1;
+        }
+    }
     void* step_fn(bool final_node) const {
         if (prm.cell_list_only) return final_node ? kt.step_cells_final : kt.step_cells;
+        const int v = variant_index();
+        if (v >= 0) return kt.step_var[v][final_node ? 1 : 0];
         return final_node ? kt.step_list_final : kt.step_list;
+    }
+    // threads per block of the step kernel (the final step always kBlock)
+    unsigned step_block(bool final_node) const {
+        if (final_node) return kBlock;
+        if (prm.variant == MD_VARIANT_BLOCK64) return 64;
+        if (prm.variant == MD_VARIANT_BLOCK128) return 128;
+        return kBlock;
+    }
+    unsigned step_grid(bool final_node) const {
+        const unsigned b = step_block(final_node);
+        return (unsigned)((a.n + b - 1) / b);
     }
 
     // The rebuild branch as stream launches.  guard = 1: every kernel returns
@@ -268,7 +292,7 @@ struct Sim : SimBase {
     int step_kernel_eager(int mode, bool final_node) {
         cudaGraphConditionalHandle none = 0;
         int has = 0;
-        MD_CUDA(launch(step_fn(final_node), grid_atoms(), kBlock, a, mode, none, has));
+        MD_CUDA(launch(step_fn(final_node), step_grid(final_node), step_block(final_node), a, mode, none, has));
         return MD_OK;
     }
 
@@ -343,7 +367,8 @@ struct Sim : SimBase {
             cudaGraphConditionalHandle nxt = (s + 1 < K) ? h[s + 1] : 0;
             int has = (s + 1 < K) ? 1 : 0;
             // only a graph's last node can meet the last step of a call
-            MD_CUDA(add_kernel(c.g, &ifn, &node, step_fn(s + 1 == K), grid_atoms(), kBlock, a, mode, nxt, has));
+            MD_CUDA(add_kernel(c.g, &ifn, &node, step_fn(s + 1 == K), step_grid(s + 1 == K), step_block(s + 1 == K), a,
+                               mode, nxt, has));
             prev = node;
         }
         MD_CUDA(cudaGraphInstantiate(&c.e, c.g, 0));
@@ -702,10 +727,11 @@ struct Sim : SimBase {
         MD_CUDA(cudaMemcpyAsync(nbr.data(), a.nbr, sizeof(int) * nbr.size(), cudaMemcpyDeviceToHost, stream));
         MD_CUDA(cudaStreamSynchronize(stream));
         int64_t np = 0, ne = 0;
+        const int cs = list_stride(a);
         for (int64_t i = 0; i < n; i++) {
-            const int* col = nbr.data() + ((size_t)(i >> 5) * a.cap) * 32 + (i & 31);
+            const int* col = nbr.data() + list_base(a, i);
             for (int m = 0; m < nn[i]; m++) {
-                int j = col[(size_t)m * 32] & kIndexMask;
+                int j = col[(size_t)m * cs] & kIndexMask;
                 if (j >= n) {
                     err = "neighbour entry out of range";
                     return MD_ECUDA;

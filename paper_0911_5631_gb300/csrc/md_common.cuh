@@ -123,7 +123,7 @@ struct alignas(16) Args {
     int cell_list_only;
     int reorder_interval;
     int shell_bins;     // lists sorted by shell bin, steps read up to the shell reach
-    int pad0;
+    int list_rows;      // list layout: 0 = a warp's 32 columns interleaved, 1 = each atom's entries contiguous
 
     double L[3], hL[3], invL[3], invW[3];
     double w[3];        // cell widths
@@ -186,6 +186,20 @@ struct alignas(16) Args {
     double* io_pos;     // [3 n] staging for set/get (user order, AoS)
     double* io_vel;     // [3 n]
 };
+
+// Entry m of atom i's neighbour list (Sec. 3.4, W_{m,i}) sits at
+// list_base(i) + m list_stride: by default the columns of a warp's 32 atoms
+// are interleaved, ((i / 32) cap + m) 32 + i % 32, so that a warp reading
+// row m of its atoms touches one 128-byte line; with list_rows each atom's
+// entries are contiguous, i cap + m (the paper's W transposed).
+template <class P>
+__host__ __device__ __forceinline__ size_t list_base(const Args<P>& a, int64_t i) {
+    return a.list_rows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (size_t)(i & 31);
+}
+template <class P>
+__host__ __device__ __forceinline__ int list_stride(const Args<P>& a) {
+    return a.list_rows ? 1 : 32;
+}
 
 // x slices of the pencil cell order (tiles of 4 x 4 cells in (y, z), each
 // taken at every c_x): the thread blocks of the warp-cooperative build.

@@ -34,6 +34,14 @@ inline int resolve_plan(const double box[3], int64_t n, double rc, double skin, 
     if (p->reorder_interval < 0) return fail("reorder_interval must be >= 0");
     if (p->nbr_capacity < 0) return fail("nbr_capacity must be >= 0");
     if (p->build_kernel < MD_BUILD_AUTO || p->build_kernel > MD_BUILD_WARP) return fail("unknown build_kernel");
+    if (p->variant != 0) {
+        const int v = p->variant;
+        if (v != MD_VARIANT_PLAIN_LOADS && v != MD_VARIANT_LIST_ROWS && v != MD_VARIANT_BLOCK64 &&
+            v != MD_VARIANT_BLOCK128)
+            return fail("variant must be 0 or a single MD_VARIANT_* flag");
+        if (p->precision != MD_PREC_MIXED || p->cell_list_only)
+            return fail("kernel variants exist for the mixed form with a neighbour list only");
+    }
     std::memset(out, 0, sizeof(*out));
     double rn = rc + skin;
     int64_t nc = 1;
@@ -117,6 +125,7 @@ void fill_args_scalars(Args<P>& a, const md_plan_t& plan, const double box[3], i
     a.cell_list_only = cell_list_only;
     a.reorder_interval = reorder_interval;
     a.shell_bins = shell_bins != 0;
+    a.list_rows = 0;
     a.dt = dt;
     a.h = 0.5 * dt;
     a.dtf = (float)dt;

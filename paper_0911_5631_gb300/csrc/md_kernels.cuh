@@ -603,7 +603,22 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int cnt, cons
 __device__ __forceinline__ float small_int_to_float(unsigned k) {  // exact for k < 2^22
     return __uint_as_float(0x4B400000u | k) - 12582912.0f;
 }
-template <bool kEnergy>
+// A gathered pair coordinate: through the read-only path (the paper's
+// texture cache, Sec. 4.4) or, for the ablation, a plain coherent load.
+template <bool kLdg>
+__device__ __forceinline__ float4 gather4(const float4* p) {
+    if constexpr (kLdg) {
+        return __ldg(p);
+    } else {
+        float4 v;
+        asm volatile("ld.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                     : "l"(p));
+        return v;
+    }
+}
+
+template <bool kEnergy, bool kLdg = true, bool kRows = false>
 __device__ __forceinline__ void forces_mixed(const Args<Mixed>& a, int cnt, const int* col, const int* rows,
                                              int staged, float qx, float qy, float qz,
                                              const float4* __restrict__ pc, AccMixed& acc) {
@@ -635,19 +650,20 @@ __device__ __forceinline__ void forces_mixed(const Args<Mixed>& a, int cnt, cons
         for (int k = 0; k < 4; k++) e[k] = (unsigned)rows[(m + k) * 32 + lane];  // rows past ns are unused
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (m + k < ns) pj[k] = __ldg(pc + min(e[k] & (unsigned)kIndexMask, nlast));
+            if (m + k < ns) pj[k] = gather4<kLdg>(pc + min(e[k] & (unsigned)kIndexMask, nlast));
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (m + k < ns) pair(e[k], pj[k]);
     }
+    constexpr int kStride = kRows ? 1 : 32;
     for (m = ns; m < cnt; m += 4) {
         unsigned e[4];
         float4 pj[4];
 #pragma unroll
-        for (int k = 0; k < 4; k++) e[k] = (m + k < cnt) ? (unsigned)__ldcs(col + (size_t)(m + k) * 32) : 0u;
+        for (int k = 0; k < 4; k++) e[k] = (m + k < cnt) ? (unsigned)__ldcs(col + (size_t)(m + k) * kStride) : 0u;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (m + k < cnt) pj[k] = __ldg(pc + min(e[k] & (unsigned)kIndexMask, nlast));
+            if (m + k < cnt) pj[k] = gather4<kLdg>(pc + min(e[k] & (unsigned)kIndexMask, nlast));
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (m + k < cnt) pair(e[k], pj[k]);
@@ -1133,7 +1149,8 @@ __device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2*
     const int i = __float_as_int(ci.w);
     int cx, cy, cz;
     unpack_cell(a.cell[i], cx, cy, cz);
-    int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
+    int* col = a.nbr + list_base(a, i);
+    const int cs = list_stride(a);
     const int cap = a.cap, n = (int)a.n;
     for (int d = 0; d < 27; d++) {
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
@@ -1152,7 +1169,7 @@ __device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2*
             if (!within_rn_fp64(a, i, j, code)) continue;
             const int e = j | (int)(code << kCodeShift);
             if (kSort && m < kBuildStage) stage[m * stride] = make_int2(e, __float_as_int(rr));
-            else if (m < cap) col[(size_t)m * 32] = e;
+            else if (m < cap) col[(size_t)m * cs] = e;
             m++;
         }
     }
@@ -1168,7 +1185,8 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
     const int i = __float_as_int(ci.w);
     int cx, cy, cz;
     unpack_cell(a.cell[i], cx, cy, cz);
-    int* col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
+    int* col = a.nbr + list_base(a, i);
+    const int cs = list_stride(a);
     const int cap = a.cap, n = (int)a.n, self = (int)s;
     const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
     const int xs[3] = {wrap_add(cx, -1, a.G[0]), cx, wrap_add(cx, 1, a.G[0])};
@@ -1203,9 +1221,9 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
                     unsure |= !(rr < lo2) && rr < hi2 && t != self;
                     if constexpr (kSort) {
                         if (take && m < kBuildStage) stage[m * stride] = make_int2(j | code, __float_as_int(rr));
-                        if (take && m >= kBuildStage && m < cap) col[(size_t)m * 32] = j | code;
+                        if (take && m >= kBuildStage && m < cap) col[(size_t)m * cs] = j | code;
                     } else {
-                        if (take && m < cap) col[(size_t)m * 32] = j | code;
+                        if (take && m < cap) col[(size_t)m * cs] = j | code;
                     }
                     m += take ? 1 : 0;
                 }
@@ -1238,11 +1256,11 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
             const unsigned inc = 1u << sh;
             nlo += b < 4 ? inc : 0u;
             nhi += b < 4 ? 0u : inc;
-            col[(size_t)dst * 32] = e.x;
+            col[(size_t)dst * cs] = e.x;
         }
     } else if (kSort) {
         const int ns = min(kept, kBuildStage);
-        for (int t = 0; t < ns; t++) col[(size_t)t * 32] = stage[t * stride].x;
+        for (int t = 0; t < ns; t++) col[(size_t)t * cs] = stage[t * stride].x;
     }
     if constexpr (kSort) {
 #pragma unroll
@@ -1335,7 +1353,7 @@ __global__ void __launch_bounds__(kWcThreads, 2) k_build_wc(Args<P> a, int guard
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     WcWarp& W = s_wc[wid];
-    const int n = (int)a.n, cap = a.cap;
+    const int n = (int)a.n, cap = a.cap, cs = list_stride(a);
     const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
     // the slice of this block and the home cell of this warp
     const int nty = (a.G[1] + 3) / 4;
@@ -1405,7 +1423,7 @@ __global__ void __launch_bounds__(kWcThreads, 2) k_build_wc(Args<P> a, int guard
                 if (b0 == 0) {
                     if (staged_home) qi = W.cand[kself];
                     i = __float_as_int(qi.w) & kIndexMask;
-                    col = a.nbr + ((size_t)(i >> 5) * (size_t)cap) * 32 + (i & 31);
+                    col = a.nbr + list_base(a, i);
                 }
                 const int kend = min(K - b0, kWcBatch);
                 for (int r = 0; r < kend; r += 32) {
@@ -1426,7 +1444,7 @@ __global__ void __launch_bounds__(kWcThreads, 2) k_build_wc(Args<P> a, int guard
                     const int dst = m + __popc(bal & lt);
                     if (take) {
                         if (dst < kWcSort) W.stage[dst] = make_int2(e, __float_as_int(rr));
-                        else if (dst < cap) col[(size_t)dst * 32] = e;
+                        else if (dst < cap) col[(size_t)dst * cs] = e;
                     }
                     m += __popc(bal);
                 }
@@ -1446,13 +1464,13 @@ __global__ void __launch_bounds__(kWcThreads, 2) k_build_wc(Args<P> a, int guard
                                M2 = __ballot_sync(kFull, (b & 4) != 0);
                 if (v) {
                     const unsigned same = V & ((b & 4) ? M2 : ~M2) & ((b & 2) ? M1 : ~M1) & ((b & 1) ? M0 : ~M0);
-                    col[(size_t)(__popc(bins_below(b, V, M0, M1, M2)) + __popc(same & lt)) * 32] = e;
+                    col[(size_t)(__popc(bins_below(b, V, M0, M1, M2)) + __popc(same & lt)) * cs] = e;
                 }
                 if (lane >= 1 && lane < kShellBins)
                     a.lim[(size_t)(lane - 1) * a.n + i] = (unsigned char)__popc(bins_below(lane, V, M0, M1, M2));
             } else {
                 const int ns = min(min(m, kWcSort), cap);
-                if (lane < ns) col[(size_t)lane * 32] = W.stage[lane].x;
+                if (lane < ns) col[(size_t)lane * cs] = W.stage[lane].x;
                 if (a.shell_bins && lane >= 1 && lane < kShellBins) a.lim[(size_t)(lane - 1) * a.n + i] = 0xff;
             }
             if (m > cap && lane == 0) {
@@ -1633,21 +1651,21 @@ __device__ __forceinline__ int list_count(const Args<P>& a, int64_t i, int k) {
 // memory (rows below the capacity always exist; unused ones are ignored)
 // and reads the number of entries of atom i that the step's shell reach
 // (from the counters) leaves to read.  Every lane of the warp must call it.
-template <class P, bool kCells>
+template <class P, bool kCells, bool kRows = false>
 __device__ __forceinline__ void stage_rows(const Args<P>& a, int64_t i, int reach, int* rows, int& cnt,
                                            int& staged, const int*& col) {
     cnt = 0;
     staged = 0;
     col = nullptr;
     if constexpr (!kCells) {
-        if ((i & ~(int64_t)31) < a.n) {  // the warp's column block exists
+        if (!kRows && (i & ~(int64_t)31) < a.n) {  // the warp's column block exists
             staged = min(a.cap, kStageRows);
             const int* blk = a.nbr + (size_t)(i >> 5) * (size_t)a.cap * 32;
             for (int c = threadIdx.x & 31; c < staged * 8; c += 32) cp_async16(rows + 4 * c, blk + 4 * c);
         }
         if (i < a.n) {
             cnt = list_count(a, i, reach);
-            col = a.nbr + ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31);
+            col = a.nbr + (kRows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31));
         }
     }
 }
@@ -1664,7 +1682,7 @@ __device__ __forceinline__ void stage_wait() {
 // KE/PE/W terms) or the next half kick, the drift into the other pair
 // buffer and the skin/2 test.  Shared by the grid kernel and the
 // per-replica engine.
-template <class P, bool kCells, bool kFinal>
+template <class P, bool kCells, bool kFinal, bool kLdg = true, bool kRows = false>
 __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, bool active, bool init, bool energy,
                                           int cnt, const int* col, const int* rows, int staged,
                                           const typename P::pos4* __restrict__ pc, typename P::pos4* pn,
@@ -1683,12 +1701,12 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
             if constexpr (kCells) forces_from_cells<P, kFinal>(a, (int)i, qx, qy, qz, pc, acc);
             else if constexpr (P::kFp64)
                 forces_from_list<P, kFinal>(a, cnt, col, rows, staged, qx, qy, qz, pc, s_shift, s_queue, acc);
-            else forces_mixed<kFinal>(a, cnt, col, rows, staged, qx, qy, qz, pc, acc);
+            else forces_mixed<kFinal, kLdg, kRows>(a, cnt, col, rows, staged, qx, qy, qz, pc, acc);
         } else {
             if constexpr (kCells) forces_from_cells<P, false>(a, (int)i, qx, qy, qz, pc, acc);
             else if constexpr (P::kFp64)
                 forces_from_list<P, false>(a, cnt, col, rows, staged, qx, qy, qz, pc, s_shift, s_queue, acc);
-            else forces_mixed<false>(a, cnt, col, rows, staged, qx, qy, qz, pc, acc);
+            else forces_mixed<false, kLdg, kRows>(a, cnt, col, rows, staged, qx, qy, qz, pc, acc);
         }
         close = acc.close != 0;
         real fx = acc.force_x(), fy = acc.force_y(), fz = acc.force_z();
@@ -1736,17 +1754,27 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
 // kModeInit (forces of a freshly loaded state); the plain variant, used for
 // every other step, carries no energy accumulators.  The last block
 // advances the counters and, in a graph, sets the next conditional rebuild.
-template <class P, bool kCells, bool kFinal>
-__global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, int mode, cudaGraphConditionalHandle next,
-                                                 int has_next) {
+//
+// The template arguments after kFinal select the kernel variants of the
+// paper's ablations (mixed list form): kB threads per block (Table 6),
+// gathers through plain coherent loads instead of the read-only path
+// (kLdg = false; the texture cache of Sec. 4.4), and the list stored with
+// each atom's entries contiguous (kRows; W transposed, no row staging).  A
+// variant with kB != kBlock serves the plain steps only: the final step,
+// which writes per-block energy partials, always runs with kBlock.
+template <class P, bool kCells, bool kFinal, int kB = kBlock, bool kLdg = true, bool kRows = false>
+__global__ void __launch_bounds__(kB, P::kFp64 ? 3 : 5 * kBlock / kB) k_step(Args<P> a, int mode,
+                                                                             cudaGraphConditionalHandle next,
+                                                                             int has_next) {
+    static_assert(!kFinal || kB == kBlock, "the final step runs with kBlock threads");
     using real = typename P::real;
     using vel = typename P::vel;
     using pos4 = typename P::pos4;
-    __shared__ double shs[kBlock / 32];
+    __shared__ double shs[kB / 32];
     constexpr bool kTable = P::kFp64 && !kCells;  // shift table and pair queue (FP64 list form)
     __shared__ pos4 s_shift[kTable ? 64 : 1];
-    __shared__ typename Queue<P>::item s_queue[kTable ? Queue<P>::kSlots * kBlock : 1];
-    __shared__ __align__(16) int s_rows[kCells ? 4 : kStageRows * kBlock];
+    __shared__ typename Queue<P>::item s_queue[kTable ? Queue<P>::kSlots * kB : 1];
+    __shared__ __align__(16) int s_rows[(kCells || kRows) ? 4 : kStageRows * kB];
     Counters* C = a.ctr;
     if constexpr (kTable) fill_shift_table<P>(a, s_shift);
     // Requests that do not depend on the counters go out first, so their
@@ -1761,8 +1789,8 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
     int cnt, staged;
     const int* col;
     int* rows = s_rows + (threadIdx.x >> 5) * (kStageRows * 32);
-    stage_rows<P, kCells>(a, i, C->reach, rows, cnt, staged, col);
-    stage_wait<kCells>();
+    stage_rows<P, kCells, kRows>(a, i, C->reach, rows, cnt, staged, col);
+    stage_wait<kCells || kRows>();
     const View vw = load_view(C);  // also orders the table fill before its use
     const int err = vw.err;
     const long long left = vw.left;
@@ -1777,8 +1805,8 @@ __global__ void __launch_bounds__(kBlock, P::kFp64 ? 3 : 5) k_step(Args<P> a, in
     bool far = false, close = false;
     double ke = 0.0, pe = 0.0, vir = 0.0;
     unsigned d2b = 0u;
-    step_atom<P, kCells, kFinal>(a, i, in, active, init, energy, cnt, col, rows, staged, pc, pn, s_shift, s_queue,
-                                 far, close, ke, pe, vir, d2b);
+    step_atom<P, kCells, kFinal, kLdg, kRows>(a, i, in, active, init, energy, cnt, col, rows, staged, pc, pn,
+                                              s_shift, s_queue, far, close, ke, pe, vir, d2b);
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
     if (__any_sync(0xffffffffu, close) && (threadIdx.x & 31) == 0) atomicOr(&C->close_flag, 1);
     warp_max_into(d2b, d2_word(a));  // the running maximum of the squared displacement
@@ -2397,8 +2425,21 @@ KernelTable<P> make_kernel_table() {
     t.rescale = (void*)k_rescale<P>;
     t.count_reads = (void*)k_count_reads<P>;
     t.spin = (void*)k_spin<P>;
-    if constexpr (!P::kFp64) t.ensemble = (void*)k_ensemble<P>;
-    else t.ensemble = nullptr;
+    if constexpr (!P::kFp64) {
+        t.ensemble = (void*)k_ensemble<P>;
+        // ablation variants of the mixed list form: {plain, final}
+        t.step_var[0][0] = (void*)k_step<P, false, false, kBlock, false, false>;  // plain loads
+        t.step_var[0][1] = (void*)k_step<P, false, true, kBlock, false, false>;
+        t.step_var[1][0] = (void*)k_step<P, false, false, kBlock, true, true>;    // W transposed
+        t.step_var[1][1] = (void*)k_step<P, false, true, kBlock, true, true>;
+        t.step_var[2][0] = (void*)k_step<P, false, false, 64, true, false>;       // 64 threads per block
+        t.step_var[2][1] = (void*)k_step<P, false, true, kBlock, true, false>;
+        t.step_var[3][0] = (void*)k_step<P, false, false, 128, true, false>;      // 128 threads per block
+        t.step_var[3][1] = (void*)k_step<P, false, true, kBlock, true, false>;
+    } else {
+        t.ensemble = nullptr;
+        for (auto& v : t.step_var) v[0] = v[1] = nullptr;
+    }
     return t;
 }
 

@@ -36,6 +36,9 @@ struct KernelTable {
     void* count_reads;
     void* spin;
     void* ensemble;  // mixed form only (nullptr for FP64)
+    // step-kernel variants of the paper's ablations, mixed list form only
+    // ({plain step, final step}; index = the MD_VARIANT_* bit position)
+    void* step_var[4][2];
 };
 
 template <class P>

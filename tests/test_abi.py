@@ -153,3 +153,23 @@ def test_ensemble_replica_bytes_needs_no_gpu(libmd):
     assert md.md_ensemble_replica_bytes(bad) == 0
     assert md.md_ensemble_replica_bytes(md.replica_desc([8.0] * 3, 410, skin=0.0)) == 0  # list form only
     assert md.md_ensemble_replica_bytes(md.replica_desc([4.0] * 3, 50)) == 0  # fewer than 3 cells
+
+
+def test_kernel_variants_and_builds_are_validated(libmd):
+    # the ablation variants exist for the mixed form with a neighbour list;
+    # one flag at a time; the build selector takes its three values
+    def plan(**kw):
+        p = md.md_default_params()
+        skin = 0.0 if kw.get("cell_list_only") else 0.4
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return md.md_plan([20.0] * 3, 1000, RC, skin, 0.005, p)
+    for v in md.VARIANTS.values():
+        plan(variant=v)
+    for bad in ({"variant": 3}, {"variant": 16}, {"variant": md.MD_VARIANT_LIST_ROWS, "precision": md.MD_PREC_FP64},
+                {"variant": md.MD_VARIANT_BLOCK64, "cell_list_only": 1}, {"build_kernel": 3}):
+        with pytest.raises(md.MDError) as e:
+            plan(**bad)
+        assert e.value.code == md.MD_EINVAL
+    for b in (md.MD_BUILD_AUTO, md.MD_BUILD_THREAD, md.MD_BUILD_WARP):
+        plan(build_kernel=b)

@@ -178,3 +178,26 @@ def test_profiled_bytes_count_the_entries_read():
     # the shell bins read fewer, but never fewer than the interacting pairs
     # (about a third of the list for this state)
     assert 0.3 * reads_off < reads_on < reads_off
+
+
+@pytest.mark.parametrize("variant", ["plain_loads", "list_rows", "block64", "block128"])
+def test_ablation_variants_give_the_same_bits(variant):
+    # The step-kernel variants of the paper's ablations (texture cache off,
+    # W transposed, 64 / 128 threads per block) change where data comes from
+    # and how work is split, not what is computed: the mixed-form trajectory
+    # across rebuilds and reorders is the default's, bit for bit, and the
+    # transposed list holds the same pairs.
+    pos, vel, L = state(4000, 0.8, 1.0, 17, jitter=0.05)
+    out = []
+    for v in ("default", variant):
+        s = md.Simulation(L, 4000, RC, 0.4, DT, reorder_interval=30, variant=v)
+        s.set_state(pos, vel)
+        s.step(150)
+        s.step(1)
+        out.append(s.get_state() + (s.measure(), s.neighbor_pairs()[0]))
+        s.close()
+    (p0, v0, m0, n0), (p1, v1, m1, n1) = out
+    assert m0["rebuilds"] == m1["rebuilds"] >= 5 and m1["reorders"] >= 4
+    assert np.array_equal(p0, p1) and np.array_equal(v0, v1)
+    assert np.array_equal(n0[np.lexsort(n0.T[::-1])], n1[np.lexsort(n1.T[::-1])])
+
