@@ -59,9 +59,11 @@ def parse():
     ap.add_argument("--no-lj", action="store_true", help="skip the Lennard-Jones line")
     ap.add_argument("--no-ablations", action="store_true",
                     help="skip the ablations (reorder interval, shell bins, kernel variants, builds)")
-    ap.add_argument("--serve-requests", type=int, default=48)
-    ap.add_argument("--serve-low-rate", type=float, default=10.0,
-                    help="arrival rate of the second, below-saturation trace")
+    ap.add_argument("--serve-requests", type=int, default=500, help="requests per serving trace")
+    ap.add_argument("--serve-big-atoms", type=int, default=65536,
+                    help="requests of at least this many atoms get a handle of their own")
+    ap.add_argument("--serve-sweep", default="0.5,0.7,0.9",
+                    help="arrival rates below saturation, as fractions of the rate the lambda=200 trace sustains")
     ap.add_argument("--eager", action="store_true", help="stream launches instead of graphs")
     ap.add_argument("--build", default="auto", choices=["auto", "thread", "warp"],
                     help="neighbour-list build kernel (md_params.build_kernel)")
@@ -288,7 +290,7 @@ def ensemble_bench(md, torch, stream, device, replicas, steps, probe):
         e.close()
 
 
-def serving_bench(md, stream, device, count, rate, budget_bytes, slice_steps):
+def serving_bench(md, stream, device, count, rate, budget_bytes, slice_steps, big_atoms=65536):
     """Replays a Poisson trace of `count` requests through the
     continuous-batching loop (paper_0911_5631_gb300.serve)."""
     from paper_0911_5631_gb300.serve import Request, Server
@@ -297,7 +299,7 @@ def serving_bench(md, stream, device, count, rate, budget_bytes, slice_steps):
     for k, (t, n, rho, T, seed, ns) in enumerate(inputs.serving_trace(count, rate=rate)):
         pos, vel, L = inputs.wca_state(n, rho, T, seed)
         reqs.append(Request(key=k, pos=pos, vel=vel, box=L, nsteps=ns, arrival=t, skin=sk, dt=DT))
-    srv = Server(budget_bytes, slice_steps=slice_steps, device=device, keep_results=False)
+    srv = Server(budget_bytes, slice_steps=slice_steps, device=device, keep_results=False, big_atoms=big_atoms)
     try:
         st = srv.serve(reqs)
     finally:
@@ -307,7 +309,8 @@ def serving_bench(md, stream, device, count, rate, budget_bytes, slice_steps):
     st.update({"workload": "wca_serving_poisson", "rate_per_s": rate, "requests_offered": count,
                "n_range": [inputs.SERVING["n_min"], inputs.SERVING["n_max"]],
                "steps_range": list(inputs.SERVING["steps"]), "slice_steps": slice_steps,
-               "budget_gb": budget_bytes / 1e9,
+               "budget_gb": budget_bytes / 1e9, "big_atoms": big_atoms,
+               "mean_atom_steps_per_request": float(np.mean([r.atoms * r.nsteps for r in reqs])),
                "offered_atom_steps_per_s": rate * float(np.mean([r.atoms * r.nsteps for r in reqs])),
                "latency": "completion - arrival (s), trace replayed in real time"})
     return st
@@ -556,8 +559,18 @@ def run_ours(args):
         lj = lj_bench(md, torch, stream, local, 5)
     serving = None
     if rank == 0 and not args.no_serving:
-        serving = [serving_bench(md, stream, local, args.serve_requests, rate, 40 << 30, 200)
-                   for rate in (inputs.SERVING["rate"], args.serve_low_rate)]
+        # the configured Poisson rate (above saturation: the queue grows and
+        # the finite trace drains at the sustained rate), then a sweep below
+        # the saturation rate that trace measured
+        top = serving_bench(md, stream, local, args.serve_requests, inputs.SERVING["rate"], 40 << 30, 200,
+                            args.serve_big_atoms)
+        serving = [top]
+        lam_sat = top["atom_steps_per_s"] / top["mean_atom_steps_per_request"]
+        for f in [float(x) for x in args.serve_sweep.split(",") if x.strip()]:
+            st = serving_bench(md, stream, local, args.serve_requests, f * lam_sat, 40 << 30, 200,
+                               args.serve_big_atoms)
+            st.update({"fraction_of_saturation": f, "saturation_rate_per_s": lam_sat})
+            serving.append(st)
     if rank == 0:
         ws_bytes = n * (12 + 24 + 12 + 32 + 4) + list_entries * 4 * 1.3
         line = {

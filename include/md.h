@@ -349,14 +349,16 @@ int md_ensemble_create(int64_t arena_bytes, int32_t max_replicas, int32_t device
                        md_ensemble** out);
 
 /* Adds a replica with positions and velocities (host, n x 3 doubles each,
- * copied before return).  Its state is loaded (wrapped, binned, listed,
- * forces computed) at the start of the next md_ensemble_run that includes
- * it.  *id receives its id.  MD_EINVAL on a bad description, MD_ENOMEM when
- * the arena or the id table is full. */
+ * copied before return; the copies do not wait for runs in flight).  Its
+ * state is loaded (wrapped, binned, listed, forces computed) at the start of
+ * the next md_ensemble_run that includes it.  *id receives its id.
+ * MD_EINVAL on a bad description, MD_ENOMEM when the arena or the id table
+ * is full. */
 int md_ensemble_add(md_ensemble* e, const md_replica_desc* d, const double* pos, const double* vel,
                     int32_t* id);
 
-/* Frees a replica's arena space and id (waits for queued work first). */
+/* Frees a replica's arena space and id (waits for the last run that
+ * included it, not for later ones). */
 int md_ensemble_remove(md_ensemble* e, int32_t id);
 
 /* Advances replicas ids[0..count) by nsteps[k] >= 0 steps each in one
@@ -370,14 +372,23 @@ int md_ensemble_run(md_ensemble* e, int32_t count, const int32_t* ids, const int
 /* Waits for the ensemble's stream. */
 int md_ensemble_sync(md_ensemble* e);
 
-/* MD_OK, or the error that stopped the replica (MD_EOVERFLOW, MD_EUNSTABLE). */
+/* Waits until at most in_flight (0 .. 7) of the runs queued so far are
+ * unfinished (0: md_ensemble_sync).  A request loop that queues the next
+ * slice before it retires the last one keeps the GPU busy with
+ * md_ensemble_wait(e, 1). */
+int md_ensemble_wait(md_ensemble* e, int32_t in_flight);
+
+/* MD_OK, or the error that stopped the replica (MD_EOVERFLOW, MD_EUNSTABLE).
+ * This, md_ensemble_measure and md_ensemble_get_state wait for the last run
+ * that included the replica, not for later runs, and copy on a stream of
+ * the ensemble's own, so they overlap runs queued after it. */
 int md_ensemble_status(md_ensemble* e, int32_t id);
 
 /* Thermodynamic state of a replica after its last run (as md_measure). */
 int md_ensemble_measure(md_ensemble* e, int32_t id, md_measure_t* out);
 
 /* Positions (wrapped) and velocities of a replica in its user order
- * (host, n x 3 doubles each). */
+ * (host, n x 3 doubles each) after its last run. */
 int md_ensemble_get_state(md_ensemble* e, int32_t id, double* pos, double* vel);
 
 /* Start and end of each listed replica's work in the last run that

@@ -171,6 +171,7 @@ SIGNATURES = [
     ("md_ensemble_remove", C.c_int, [_H, C.c_int32]),
     ("md_ensemble_run", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_void_p]),
     ("md_ensemble_sync", C.c_int, [_H]),
+    ("md_ensemble_wait", C.c_int, [_H, C.c_int32]),
     ("md_ensemble_status", C.c_int, [_H, C.c_int32]),
     ("md_ensemble_measure", C.c_int, [_H, C.c_int32, C.POINTER(md_measure_t)]),
     ("md_ensemble_get_state", C.c_int, [_H, C.c_int32, C.c_void_p, C.c_void_p]),
@@ -520,6 +521,10 @@ class Ensemble:
 
     def sync(self):
         _ens_check(lib().md_ensemble_sync(self.e), self.e)
+
+    def wait(self, in_flight=1):
+        """Blocks until at most `in_flight` queued runs are unfinished."""
+        _ens_check(lib().md_ensemble_wait(self.e, int(in_flight)), self.e)
 
     def status(self, rid) -> int:
         return int(lib().md_ensemble_status(self.e, int(rid)))

@@ -154,10 +154,17 @@ struct Replica {
 
 }  // namespace
 
+constexpr int kRunEvents = 8;  // events of the most recent runs, reused in a ring
+
 struct md_ensemble {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // Host-side calls on one replica (add, measure, status, get_state) run
+    // their copies on a stream of their own after an event of the replica's
+    // last run, so that they overlap the runs queued after it.
+    cudaStream_t xs = nullptr;
+    cudaEvent_t run_ev[kRunEvents] = {};
     char* arena = nullptr;
     int64_t arena_bytes = 0;
     Arena alloc;
@@ -254,9 +261,21 @@ int fetch_jobs(md_ensemble* e) {
     return MD_OK;
 }
 
+// The event recorded after run r (1-based).  Once kRunEvents later runs
+// have been queued it holds a later run, whose completion implies run r's.
+cudaEvent_t run_event(md_ensemble* e, int r) { return e->run_ev[(r - 1) % kRunEvents]; }
+
+// Orders the transfer stream after the last run that included the replica.
+int after_last_run(md_ensemble* e, const Replica& rp) {
+    if (rp.last_run >= 1) ENS_CUDA(cudaStreamWaitEvent(e->xs, run_event(e, rp.last_run), 0));
+    return MD_OK;
+}
+
 int read_counters(md_ensemble* e, const Replica& rp, Counters* c) {
-    ENS_CUDA(cudaMemcpyAsync(c, rp.a.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, e->stream));
-    ENS_CUDA(cudaStreamSynchronize(e->stream));
+    int r = after_last_run(e, rp);
+    if (r) return r;
+    ENS_CUDA(cudaMemcpyAsync(c, rp.a.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, e->xs));
+    ENS_CUDA(cudaStreamSynchronize(e->xs));
     return MD_OK;
 }
 
@@ -327,6 +346,7 @@ int launch_run(md_ensemble* e, const std::vector<EnsJob>& jobs, int nteam, int b
     e->last_njobs = nj;
     e->jobs_valid = false;
     e->runs++;
+    ENS_CUDA(cudaEventRecord(run_event(e, e->runs), e->stream));
     return MD_OK;
 }
 
@@ -420,6 +440,15 @@ int md_ensemble_create(int64_t arena_bytes, int32_t max_replicas, int32_t device
         return code;
     };
     e->kt = make_kernel_table<Mixed>();
+    if (cudaStreamCreateWithFlags(&e->xs, cudaStreamNonBlocking) != cudaSuccess) {
+        e->err = "cudaStreamCreateWithFlags failed";
+        return fail(MD_ECUDA);
+    }
+    for (auto& ev : e->run_ev)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+            e->err = "cudaEventCreate failed";
+            return fail(MD_ECUDA);
+        }
     if (stream) {
         e->stream = (cudaStream_t)stream;
     } else {
@@ -512,19 +541,22 @@ int md_ensemble_add(md_ensemble* e, const md_replica_desc* d, const double* pos,
         if (slot == (int)e->reps.size() - 1) e->reps.pop_back();
         return code;
     };
-    cudaError_t c1 = cudaMemcpyAsync(rp.a.io_pos, pos, bytes, cudaMemcpyHostToDevice, e->stream);
-    cudaError_t c2 = cudaMemcpyAsync(rp.a.io_vel, vel, bytes, cudaMemcpyHostToDevice, e->stream);
-    cudaError_t c3 = cudaMemsetAsync(rp.a.count, 0, sizeof(int) * (size_t)rp.a.ncells, e->stream);
-    cudaError_t c4 = cudaMemsetAsync(rp.a.nn, 0, sizeof(int) * (size_t)rp.a.n, e->stream);
-    cudaError_t c5 = cudaMemsetAsync(rp.a.ctr, 0, sizeof(Counters), e->stream);
-    cudaError_t c6 = cudaMemcpyAsync(e->d_args + slot, &rp.a, sizeof(A), cudaMemcpyHostToDevice, e->stream);
+    // On the transfer stream: the arena space and the table slot belong to
+    // no queued run (a removed replica's last run had finished), so the
+    // copies may overlap the runs in flight.
+    cudaError_t c1 = cudaMemcpyAsync(rp.a.io_pos, pos, bytes, cudaMemcpyHostToDevice, e->xs);
+    cudaError_t c2 = cudaMemcpyAsync(rp.a.io_vel, vel, bytes, cudaMemcpyHostToDevice, e->xs);
+    cudaError_t c3 = cudaMemsetAsync(rp.a.count, 0, sizeof(int) * (size_t)rp.a.ncells, e->xs);
+    cudaError_t c4 = cudaMemsetAsync(rp.a.nn, 0, sizeof(int) * (size_t)rp.a.n, e->xs);
+    cudaError_t c5 = cudaMemsetAsync(rp.a.ctr, 0, sizeof(Counters), e->xs);
+    cudaError_t c6 = cudaMemcpyAsync(e->d_args + slot, &rp.a, sizeof(A), cudaMemcpyHostToDevice, e->xs);
     if (c1 || c2 || c3 || c4 || c5 || c6) {
         e->err = "copying the replica's state failed";
         return undo(MD_ECUDA);
     }
-    // the host copy of the arguments (pageable) must outlive the copy:
-    // finish it before the local goes away
-    if (cudaStreamSynchronize(e->stream) != cudaSuccess) {
+    // the host copy of the arguments (pageable) must outlive the copy, and
+    // the next run must see the state: finish them before returning
+    if (cudaStreamSynchronize(e->xs) != cudaSuccess) {
         e->err = "cudaStreamSynchronize failed";
         return undo(MD_ECUDA);
     }
@@ -538,8 +570,10 @@ int md_ensemble_remove(md_ensemble* e, int32_t id) {
     int r = bad_id(e, id);
     if (r) return r;
     EnsDev dg(e->device);
-    ENS_CUDA(cudaStreamSynchronize(e->stream));
     Replica& rp = e->reps[id];
+    // its memory is free once its last run has finished (later runs do
+    // not touch it)
+    if (rp.last_run >= 1) ENS_CUDA(cudaEventSynchronize(run_event(e, rp.last_run)));
     e->alloc.release(rp.off, rp.bytes);
     rp = Replica();
     return MD_OK;
@@ -559,6 +593,22 @@ int md_ensemble_sync(md_ensemble* e) {
     if (!e) return MD_EINVAL;
     EnsDev dg(e->device);
     ENS_CUDA(cudaStreamSynchronize(e->stream));
+    return MD_OK;
+}
+
+int md_ensemble_wait(md_ensemble* e, int32_t in_flight) {
+    if (!e) return MD_EINVAL;
+    if (in_flight < 0 || in_flight >= kRunEvents) {
+        e->err = "in_flight must be in 0..7";
+        return MD_EINVAL;
+    }
+    EnsDev dg(e->device);
+    if (in_flight == 0) {
+        ENS_CUDA(cudaStreamSynchronize(e->stream));
+        return MD_OK;
+    }
+    const int r = e->runs - in_flight;
+    if (r >= 1) ENS_CUDA(cudaEventSynchronize(run_event(e, r)));
     return MD_OK;
 }
 
@@ -632,13 +682,15 @@ int md_ensemble_get_state(md_ensemble* e, int32_t id, double* pos, double* vel) 
         return MD_ESTATE;
     }
     EnsDev dg(e->device);
+    r = after_last_run(e, rp);
+    if (r) return r;
     void* args[] = {(void*)&rp.a};
     unsigned grid = (unsigned)((rp.a.n + kBlock - 1) / kBlock);
-    ENS_CUDA(cudaLaunchKernel(e->kt.get_state, dim3(grid), dim3(kBlock), args, 0, e->stream));
+    ENS_CUDA(cudaLaunchKernel(e->kt.get_state, dim3(grid), dim3(kBlock), args, 0, e->xs));
     size_t bytes = sizeof(double) * 3 * (size_t)rp.a.n;
-    ENS_CUDA(cudaMemcpyAsync(pos, rp.a.io_pos, bytes, cudaMemcpyDeviceToHost, e->stream));
-    ENS_CUDA(cudaMemcpyAsync(vel, rp.a.io_vel, bytes, cudaMemcpyDeviceToHost, e->stream));
-    ENS_CUDA(cudaStreamSynchronize(e->stream));
+    ENS_CUDA(cudaMemcpyAsync(pos, rp.a.io_pos, bytes, cudaMemcpyDeviceToHost, e->xs));
+    ENS_CUDA(cudaMemcpyAsync(vel, rp.a.io_vel, bytes, cudaMemcpyDeviceToHost, e->xs));
+    ENS_CUDA(cudaStreamSynchronize(e->xs));
     return MD_OK;
 }
 
@@ -758,6 +810,12 @@ void md_ensemble_destroy(md_ensemble* e) {
     if (!e) return;
     EnsDev dg(e->device);
     if (e->stream) cudaStreamSynchronize(e->stream);
+    if (e->xs) {
+        cudaStreamSynchronize(e->xs);
+        cudaStreamDestroy(e->xs);
+    }
+    for (auto& ev : e->run_ev)
+        if (ev) cudaEventDestroy(ev);
     if (e->arena) cudaFree(e->arena);
     if (e->d_args) cudaFree(e->d_args);
     if (e->d_jobs) cudaFree(e->d_jobs);

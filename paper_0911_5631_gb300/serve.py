@@ -57,6 +57,7 @@ class Request:
     thread: object = None         # worker of a big request
     solo_need: int = 0
     left: int = 0
+    last_launch: int = 0          # ensemble slice that ran the last steps
     atoms: int = field(init=False)
 
     def __post_init__(self):
@@ -171,8 +172,11 @@ class Server:
             self.queue.pop(0)
             req.admitted = now
 
-    def _retire(self, now: float):
-        for rid in [r for r, q in self.active.items() if q.left == 0]:
+    def _retire(self, now: float, finished: int):
+        """Retires the requests whose last slice is among the first
+        `finished` launches (all finished on the device): the per-replica
+        calls below then return without waiting for the slice in flight."""
+        for rid in [r for r, q in self.active.items() if q.left == 0 and q.last_launch <= finished]:
             req = self.active.pop(rid)
             req.status = self.ens.status(rid)
             if req.status == MD_OK:
@@ -185,13 +189,14 @@ class Server:
                 self.done.append(req)
 
     def step(self, now: float) -> bool:
-        """One scheduling iteration at time `now`: admit, run one slice of
-        every active request, retire the finished ones.  Returns False when
-        there was nothing to run."""
+        """One scheduling iteration at time `now`: admit, queue one slice of
+        every active request that has steps left.  Returns False when there
+        was nothing to run.  Requests whose steps are all queued are retired
+        by _retire once their last slice has finished."""
         self._admit(now)
-        if not self.active:
+        ids = [r for r, q in self.active.items() if q.left > 0]
+        if not ids:
             return False
-        ids = list(self.active.keys())
         # about the same work per block in one slice: small replicas take
         # more steps than big ones (at least slice_steps when they can), so
         # no slice waits long for its largest member
@@ -202,13 +207,18 @@ class Server:
             if q.atoms >= self.team_atoms:
                 k = max(1, (self.slice_atom_steps * self.team_blocks) // q.atoms)
             steps.append(min(q.left, k))
+        # queue the slice and return at once: the requests that finished in
+        # the previous slice are retired while this one runs, and the next
+        # iteration waits for the previous slice only (one run in flight
+        # behind the newest), so the GPU never idles for the bookkeeping
         self.ens.run(ids, steps)
-        self.ens.sync()
         with self._lock:
             self.launches += 1
             for r, s in zip(ids, steps):
                 q = self.active[r]
                 q.left -= s
+                if q.left == 0:
+                    q.last_launch = self.launches
                 self.atom_steps += q.atoms * s
         return True
 
@@ -230,9 +240,13 @@ class Server:
                 self.submit(pending[k])
                 k += 1
             ran = self.step(now)
-            now = clock() - t0
-            self._retire(now)
-            if not ran:  # nothing on the ensemble: wait for an arrival or a worker
+            if ran:  # the slice before the one just queued has finished
+                self.ens.wait(1)
+                self._retire(clock() - t0, self.launches - 1)
+            else:  # nothing left to queue: finish what runs, then wait for an arrival or a worker
+                self.ens.wait(0)
+                self._retire(clock() - t0, self.launches)
+                now = clock() - t0
                 nxt = pending[k].arrival - now if k < len(pending) else 0.002
                 time.sleep(max(0.0, min(nxt, 0.002)))
         for q in self.done:

@@ -47,6 +47,9 @@ class StandIn:
     def sync(self):
         pass
 
+    def wait(self, in_flight=1):
+        self.waits = getattr(self, "waits", 0) + 1
+
     def status(self, rid):
         return md.MD_OK
 
