@@ -289,12 +289,17 @@ struct Sim : SimBase {
         return MD_OK;
     }
 
-    int step_kernel_eager(int mode, bool final_node) {
+    // The step kernel, then (kStepTailNode) its one-warp closing kernel; the
+    // event `after_step`, when given, is recorded between the two.
+    int step_kernel_eager(int mode, bool final_node, cudaEvent_t after_step = nullptr) {
         cudaGraphConditionalHandle none = 0;
         int has = 0;
         MD_CUDA(launch(step_fn(final_node), step_grid(final_node), step_block(final_node), a, mode, none, has));
+        if (after_step) MD_CUDA(cudaEventRecord(after_step, stream));
+        if (kStepTailNode) MD_CUDA(launch(tail_fn(final_node), 1, 32, a, mode, none, has));
         return MD_OK;
     }
+    void* tail_fn(bool final_node) const { return final_node ? kt.step_tail_final : kt.step_tail; }
 
     // ---- graphs ----------------------------------------------------------
 
@@ -369,6 +374,10 @@ struct Sim : SimBase {
             // only a graph's last node can meet the last step of a call
             MD_CUDA(add_kernel(c.g, &ifn, &node, step_fn(s + 1 == K), step_grid(s + 1 == K), step_block(s + 1 == K), a,
                                mode, nxt, has));
+            if (kStepTailNode) {
+                cudaGraphNode_t stepn = node;
+                MD_CUDA(add_kernel(c.g, &stepn, &node, tail_fn(s + 1 == K), 1, 32, a, mode, nxt, has));
+            }
             prev = node;
         }
         MD_CUDA(cudaGraphInstantiate(&c.e, c.g, 0));
@@ -401,12 +410,12 @@ struct Sim : SimBase {
             for (int64_t b = 0; b < nb; b++) {
                 MD_CUDA(cudaGraphLaunch(big.e, stream));
                 graph_launches++;
-                launches += 1 + kChunk;
+                launches += 1 + kChunk * (kStepTailNode ? 2 : 1);
             }
             for (int64_t b = 0; b < rem; b++) {
                 MD_CUDA(cudaGraphLaunch(one.e, stream));
                 graph_launches++;
-                launches += 2;
+                launches += kStepTailNode ? 3 : 2;
             }
         } else {
             if (profiling && (int64_t)ev.size() < 4 * nsteps) {
@@ -439,9 +448,8 @@ struct Sim : SimBase {
                     MD_CUDA(launch(kt.count_reads, grid_atoms(), kBlock, a));
                     MD_CUDA(cudaEventRecord(ev[4 * s], stream));
                 }
-                r = step_kernel_eager(kModeAuto, s + 1 == nsteps);
+                r = step_kernel_eager(kModeAuto, s + 1 == nsteps, profiling ? ev[4 * s + 1] : nullptr);
                 if (r) return r;
-                if (profiling) MD_CUDA(cudaEventRecord(ev[4 * s + 1], stream));
             }
             if (profiling) {
                 MD_CUDA(cudaStreamSynchronize(stream));

@@ -9,6 +9,10 @@ namespace md {
 
 // Threads per block for every per-atom / per-slot kernel.
 constexpr int kBlock = 256;
+// The step's closing work (counters, rebuild decision, next conditional
+// node) runs as a one-warp kernel after the step kernel rather than in the
+// step kernel's last block.
+constexpr bool kStepTailNode = true;
 constexpr int kStageRows = 12;  // neighbour-list rows a step-kernel warp copies to shared memory
 // The skin shell [r_c, r_n) is cut into kShellBins bins of width skin /
 // kShellBins.  The build sorts each atom's entries by the bin of their

@@ -1746,6 +1746,11 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
     }
 }
 
+template <class P>
+__device__ __forceinline__ void close_step(const Args<P>& a, int err, long long left, int par, bool init, bool last,
+                                           bool misplaced, bool active, cudaGraphConditionalHandle next,
+                                           int has_next);
+
 // Force + integration kernel (Sec. 3.1 (c)-(e) of one step and (a) of the
 // next).  A full step: forces f_n, v_n = v_{n-1/2} + f_n dt/2,
 // v_{n+1/2} = v_n + f_n dt/2, o += v_{n+1/2} dt into the other pair buffer
@@ -1822,50 +1827,80 @@ __global__ void __launch_bounds__(kB, P::kFp64 ? 3 : 5 * kBlock / kB) k_step(Arg
             }
         }
     }
-    if (last_block_done(C)) {
-        // The counters this block reads go out together (one round trip to
-        // L2 on the step's serial tail); every other block has finished.
-        int err0 = 0, close0 = 0;
-        unsigned far0 = 0u;
-        long long step0 = 0, since0 = 0;
-        if (threadIdx.x == 0) {
-            err0 = C->error;
-            close0 = C->close_flag;
-            far0 = C->far_flag;
-            step0 = C->step;
-            since0 = C->since_reorder;
-        }
-        const unsigned d2 = threadIdx.x < 32 ? d2_gather_warp(a) : 0u;
-        if (threadIdx.x == 0) {
-            int need = 0;
-            int errn = err0;
-            if (misplaced && err == 0) errn |= kErrInternal;
-            if (close0) errn |= kErrClose;
-            if (errn != err0) C->error = errn;
-            if (close0) C->close_flag = 0;
-            if (active && !init) {
-                C->steps_left = left - 1;
-                C->step = step0 + 1;
-                C->since_reorder = since0 + 1;
-                if (!last) {
-                    C->parity = par ^ 1;
-                    // the rebuild decision of decide_rebuild, on the values read above
-                    need = (far0 != 0u) || a.cell_list_only;
-                    C->rebuild_flag = need;
-                    C->reorder_now = need && a.reorder_interval > 0 && since0 + 1 >= a.reorder_interval;
-                } else {
-                    C->rebuild_flag = 0;
-                }
-                C->far_flag = 0u;
-            } else if (!init) {
-                C->far_flag = 0u;
-            }
-            C->d2max = d2;
-            C->reach = shell_reach(a, d2);
-            if (has_next) cudaGraphSetConditional(next, need ? 1u : 0u);
-            C->ticket = 0;
-        }
+    if constexpr (!kStepTailNode) {
+        if (last_block_done(C)) close_step<P>(a, err, left, par, init, last, misplaced, active, next, has_next);
     }
+}
+
+// The step's closing work (Sec. 3.1 (b) for the next step): error bits,
+// counters, the rebuild decision and the shell reach, and in a graph the
+// next conditional rebuild node.  Every lane of warp 0 of one block calls
+// it after all of the step's blocks have finished.
+template <class P>
+__device__ __forceinline__ void close_step(const Args<P>& a, int err, long long left, int par, bool init, bool last,
+                                           bool misplaced, bool active, cudaGraphConditionalHandle next,
+                                           int has_next) {
+    Counters* C = a.ctr;
+    // the counters read here go out together (one round trip to L2 on the
+    // step's serial tail)
+    int err0 = 0, close0 = 0;
+    unsigned far0 = 0u;
+    long long step0 = 0, since0 = 0;
+    if (threadIdx.x == 0) {
+        err0 = C->error;
+        close0 = C->close_flag;
+        far0 = C->far_flag;
+        step0 = C->step;
+        since0 = C->since_reorder;
+    }
+    const unsigned d2 = threadIdx.x < 32 ? d2_gather_warp(a) : 0u;
+    if (threadIdx.x == 0) {
+        int need = 0;
+        int errn = err0;
+        if (misplaced && err == 0) errn |= kErrInternal;
+        if (close0) errn |= kErrClose;
+        if (errn != err0) C->error = errn;
+        if (close0) C->close_flag = 0;
+        if (active && !init) {
+            C->steps_left = left - 1;
+            C->step = step0 + 1;
+            C->since_reorder = since0 + 1;
+            if (!last) {
+                C->parity = par ^ 1;
+                // the rebuild decision of decide_rebuild, on the values read above
+                need = (far0 != 0u) || a.cell_list_only;
+                C->rebuild_flag = need;
+                C->reorder_now = need && a.reorder_interval > 0 && since0 + 1 >= a.reorder_interval;
+            } else {
+                C->rebuild_flag = 0;
+            }
+            C->far_flag = 0u;
+        } else if (!init) {
+            C->far_flag = 0u;
+        }
+        C->d2max = d2;
+        C->reach = shell_reach(a, d2);
+        if (has_next) cudaGraphSetConditional(next, need ? 1u : 0u);
+        C->ticket = 0;
+    }
+}
+
+// The step's closing work as a node of its own (one warp), run after the
+// step kernel: the step's blocks then end without a block barrier or a
+// ticket, and the serial tail leaves the step kernel.  It sees the counters
+// the step's blocks saw (only this kernel changes them during a step).
+template <class P, bool kFinal>
+__global__ void k_step_tail(Args<P> a, int mode, cudaGraphConditionalHandle next, int has_next) {
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    Counters* C = a.ctr;
+    const int err = __ldcg(&C->error);
+    const long long left = __ldcg(&C->steps_left);
+    const int par = __ldcg(&C->parity);
+    const bool init = kFinal && (mode == kModeInit);
+    const bool last = kFinal && !init && left == 1;
+    const bool misplaced = !kFinal && left == 1;
+    const bool active = init || (err == 0 && left > 0 && !misplaced);
+    close_step<P>(a, err, left, par, init, last, misplaced, active, next, has_next);
 }
 
 // Profiling aid, not part of a step: adds to ctr->list_reads the number of
@@ -2411,6 +2446,8 @@ KernelTable<P> make_kernel_table() {
     t.rebuild_done = (void*)k_rebuild_done<P>;
     t.cond = (void*)k_cond<P>;
     t.kickdrift = (void*)k_kickdrift<P>;
+    t.step_tail = (void*)k_step_tail<P, false>;
+    t.step_tail_final = (void*)k_step_tail<P, true>;
     t.step_list = (void*)k_step<P, false, false>;
     t.step_list_final = (void*)k_step<P, false, true>;
     t.step_cells = (void*)k_step<P, true, false>;

@@ -21,6 +21,8 @@ struct KernelTable {
     void* rebuild_done;
     void* cond;
     void* kickdrift;
+    void* step_tail;        // the step's closing work as a node of its own
+    void* step_tail_final;
     void* step_list;
     void* step_list_final;
     void* step_cells;
