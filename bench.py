@@ -354,7 +354,8 @@ ABLATIONS = [
     # (reorder interval; 0 = never after the load), reading every list entry
     # at every step as the paper does (shell bins off), the texture-cache
     # remark of Sec. 4.4 (plain loads), W transposed, Table 6 (threads per
-    # block of the force kernel), and the warp-cooperative build
+    # block of the force kernel: 64 and 256 against the default 128), and
+    # the warp-cooperative build
     ("reorder_0", {"reorder_interval": 0}),
     ("reorder_20", {"reorder_interval": 20}),
     ("reorder_100 (default)", {"reorder_interval": 100}),
@@ -363,7 +364,7 @@ ABLATIONS = [
     ("plain_loads", {"variant": "plain_loads"}),
     ("w_transposed", {"variant": "list_rows"}),
     ("block_64", {"variant": "block64"}),
-    ("block_128", {"variant": "block128"}),
+    ("block_256", {"variant": "block256"}),
     ("warp_build", {"build": "warp"}),
 ]
 

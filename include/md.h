@@ -120,8 +120,8 @@ typedef struct md_params {
                                      i * capacity + m) instead of a warp's 32
                                      columns interleaved                      */
 #define MD_VARIANT_BLOCK64     4  /* force + integrate kernel with 64 threads
-                                     per block (Table 6; default 256)         */
-#define MD_VARIANT_BLOCK128    8  /* ... with 128 threads per block           */
+                                     per block (Table 6; default 128)         */
+#define MD_VARIANT_BLOCK256    8  /* ... with 256 threads per block           */
 
 #define MD_BUILD_AUTO   0  /* the faster build on the workloads measured:
                               MD_BUILD_THREAD                                 */

@@ -43,9 +43,9 @@ _BUILD = {"auto": MD_BUILD_AUTO, "thread": MD_BUILD_THREAD, "warp": MD_BUILD_WAR
 MD_VARIANT_PLAIN_LOADS = 1
 MD_VARIANT_LIST_ROWS = 2
 MD_VARIANT_BLOCK64 = 4
-MD_VARIANT_BLOCK128 = 8
+MD_VARIANT_BLOCK256 = 8
 VARIANTS = {"default": 0, "plain_loads": MD_VARIANT_PLAIN_LOADS, "list_rows": MD_VARIANT_LIST_ROWS,
-            "block64": MD_VARIANT_BLOCK64, "block128": MD_VARIANT_BLOCK128}
+            "block64": MD_VARIANT_BLOCK64, "block256": MD_VARIANT_BLOCK256}
 
 WCA_RC = 2.0 ** (1.0 / 6.0)
 

@@ -251,7 +251,7 @@ struct Sim : SimBase {
             case MD_VARIANT_PLAIN_LOADS: return 0;
             case MD_VARIANT_LIST_ROWS: return 1;
             case MD_VARIANT_BLOCK64: return 2;
-            case MD_VARIANT_BLOCK128: return 3;
+            case MD_VARIANT_BLOCK256: return 3;
             default: return -1;
         }
     }
@@ -263,10 +263,10 @@ struct Sim : SimBase {
     }
     // threads per block of the step kernel (the final step always kBlock)
     unsigned step_block(bool final_node) const {
-        if (final_node) return kBlock;
+        if (final_node || P::kFp64 || prm.cell_list_only) return kBlock;
         if (prm.variant == MD_VARIANT_BLOCK64) return 64;
-        if (prm.variant == MD_VARIANT_BLOCK128) return 128;
-        return kBlock;
+        if (prm.variant == MD_VARIANT_BLOCK256) return 256;
+        return kStepBlockMixed;
     }
     unsigned step_grid(bool final_node) const {
         const unsigned b = step_block(final_node);

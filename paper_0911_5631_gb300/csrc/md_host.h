@@ -37,7 +37,7 @@ inline int resolve_plan(const double box[3], int64_t n, double rc, double skin, 
     if (p->variant != 0) {
         const int v = p->variant;
         if (v != MD_VARIANT_PLAIN_LOADS && v != MD_VARIANT_LIST_ROWS && v != MD_VARIANT_BLOCK64 &&
-            v != MD_VARIANT_BLOCK128)
+            v != MD_VARIANT_BLOCK256)
             return fail("variant must be 0 or a single MD_VARIANT_* flag");
         if (p->precision != MD_PREC_MIXED || p->cell_list_only)
             return fail("kernel variants exist for the mixed form with a neighbour list only");

@@ -18,8 +18,10 @@
 // GB300 note.  The FP64 pipe issues about two instructions per clock per SM
 // here, and so do the hardware conversions float<->int64 and
 // double<->float.  The mixed form therefore keeps FP64 to the three
-// position-update FMAs per atom and step, and does its conversions on the
-// FP32 and integer pipes (namespace cvt, struct Fix).
+// position-update FMAs per atom and step, and does most of its conversions
+// on the FP32 and integer pipes (namespace cvt, struct Fix); the step
+// kernel, whose integer pipe is the busiest, converts the displacement to
+// FP32 on the FP64 pipe instead.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,6 +72,18 @@ struct View {
     int par;
     long long left;
 };
+// The same view read by each warp on its own (lane 0 reads, a shuffle
+// spreads it): no block barrier.
+__device__ __forceinline__ View load_view_warp(const Counters* C) {
+    int e = 0, p = 0;
+    long long l = 0;
+    if ((threadIdx.x & 31) == 0) {
+        e = C->error;
+        p = C->parity;
+        l = C->steps_left;
+    }
+    return View{__shfl_sync(0xffffffffu, e, 0), __shfl_sync(0xffffffffu, p, 0), __shfl_sync(0xffffffffu, l, 0)};
+}
 __device__ __forceinline__ View load_view(const Counters* C) {
     __shared__ int s_err, s_par;
     __shared__ long long s_left;
@@ -386,7 +400,9 @@ __device__ __forceinline__ double drift(double o, double v, double dt) { return 
 // Pair coordinate after a drift and the squared displacement in the pair
 // precision (the skin/2 test).
 __device__ __forceinline__ float moved(float pb, double o, float& p) {
-    float d = cvt::f32(o);
+    // the hardware conversion (on the FP64 pipe): the step kernel is bound
+    // by the integer pipe, which the bit-level conversion would load further
+    float d = __double2float_rn(o);
     p = pb + d;
     return d * d;
 }
@@ -1796,7 +1812,8 @@ __global__ void __launch_bounds__(kB, P::kFp64 ? 3 : 5 * kBlock / kB) k_step(Arg
     int* rows = s_rows + (threadIdx.x >> 5) * (kStageRows * 32);
     stage_rows<P, kCells, kRows>(a, i, C->reach, rows, cnt, staged, col);
     stage_wait<kCells || kRows>();
-    const View vw = load_view(C);  // also orders the table fill before its use
+    // the FP64 list form's block barrier also orders the table fill before its use
+    const View vw = (kTable || !kStepTailNode || !kWarpView) ? load_view(C) : load_view_warp(C);
     const int err = vw.err;
     const long long left = vw.left;
     const int par = vw.par;
@@ -2448,7 +2465,8 @@ KernelTable<P> make_kernel_table() {
     t.kickdrift = (void*)k_kickdrift<P>;
     t.step_tail = (void*)k_step_tail<P, false>;
     t.step_tail_final = (void*)k_step_tail<P, true>;
-    t.step_list = (void*)k_step<P, false, false>;
+    if constexpr (P::kFp64) t.step_list = (void*)k_step<P, false, false>;
+    else t.step_list = (void*)k_step<P, false, false, kStepBlockMixed>;
     t.step_list_final = (void*)k_step<P, false, true>;
     t.step_cells = (void*)k_step<P, true, false>;
     t.step_cells_final = (void*)k_step<P, true, true>;
@@ -2465,13 +2483,13 @@ KernelTable<P> make_kernel_table() {
     if constexpr (!P::kFp64) {
         t.ensemble = (void*)k_ensemble<P>;
         // ablation variants of the mixed list form: {plain, final}
-        t.step_var[0][0] = (void*)k_step<P, false, false, kBlock, false, false>;  // plain loads
+        t.step_var[0][0] = (void*)k_step<P, false, false, kStepBlockMixed, false, false>;  // plain loads
         t.step_var[0][1] = (void*)k_step<P, false, true, kBlock, false, false>;
-        t.step_var[1][0] = (void*)k_step<P, false, false, kBlock, true, true>;    // W transposed
+        t.step_var[1][0] = (void*)k_step<P, false, false, kStepBlockMixed, true, true>;    // W transposed
         t.step_var[1][1] = (void*)k_step<P, false, true, kBlock, true, true>;
         t.step_var[2][0] = (void*)k_step<P, false, false, 64, true, false>;       // 64 threads per block
         t.step_var[2][1] = (void*)k_step<P, false, true, kBlock, true, false>;
-        t.step_var[3][0] = (void*)k_step<P, false, false, 128, true, false>;      // 128 threads per block
+        t.step_var[3][0] = (void*)k_step<P, false, false, 256, true, false>;      // 256 threads per block
         t.step_var[3][1] = (void*)k_step<P, false, true, kBlock, true, false>;
     } else {
         t.ensemble = nullptr;
