@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--ens-steps", type=int, default=inputs.ENSEMBLE["steps"])
     ap.add_argument("--no-serving", action="store_true", help="skip the serving-trace lines")
     ap.add_argument("--no-lj", action="store_true", help="skip the Lennard-Jones line")
+    ap.add_argument("--drift", action="store_true",
+                    help="only the 8M-atom energy-drift runs (10^5 steps at each (rho, T) pairing, FP64 oracle "
+                         "segments every 10^4 steps); prints their JSON summary")
+    ap.add_argument("--drift-steps", type=int, default=100000)
+    ap.add_argument("--drift-every", type=int, default=10000)
     ap.add_argument("--no-ablations", action="store_true",
                     help="skip the ablations (reorder interval, shell bins, kernel variants, builds)")
     ap.add_argument("--serve-requests", type=int, default=500, help="requests per serving trace")
@@ -604,9 +609,85 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+DRIFT_WORKLOADS = ["wca_fcc128_n8m_rho0.6_T0.7", "wca_fcc128_n8m_rho0.6_T2.0", "wca_fcc128_n8m_rho1.0_T0.7",
+                   "wca_fcc128_n8m_rho1.0_T2.0"]
+
+
+def drift_runs(args):
+    """The 8M-atom mixed-form runs: for each (rho, T) pairing, 500 untimed
+    steps from the lattice, then `--drift-steps` steps with the total energy
+    per atom sampled every 100 steps; every `--drift-every` steps the FP64
+    oracle (all host cores) runs 5 steps from the GPU's state and the GPU's
+    own next 5 steps are compared with it (velocity and position RMS
+    against the trajectory tolerance of the parity tests).  Drift is
+    |<e_tot>_{last 1000 steps} - <e_tot>_{steps 1000-2000}| per atom (block
+    means of the samples), beside the largest excursion of e_tot per atom."""
+    import torch
+    import oracle
+    import paper_0911_5631_gb300 as md
+    torch.cuda.set_device(0)
+    out = []
+    k = 5
+    for wl in DRIFT_WORKLOADS:
+        cfg = inputs.WORKLOADS[wl]
+        n = cfg["n"]
+        pos, vel, L = inputs.wca_state(n, cfg["rho"], cfg["T"], cfg["seed"])
+        s = md.Simulation(L, n, RC, cfg["skin"], DT, precision="mixed", reorder_interval=100, device=0)
+        t_wall = time.perf_counter()
+        segs, samples = [], []
+        try:
+            s.set_state(pos, vel)
+            s.step(500)
+            done = 0
+            while done < args.drift_steps:
+                if done % args.drift_every == 0:
+                    p, v = s.get_state()
+                    t0 = time.perf_counter()
+                    ref = oracle.run(p, v, L, RC, cfg["skin"], DT, k, record=False, threaded=True)
+                    t_orc = time.perf_counter() - t0
+                    s.step(k)
+                    p2, v2 = s.get_state()
+                    f_rms = float(np.sqrt(np.mean(ref["f"] ** 2)))
+                    dv_tol = 10.0 * k * DT * 1e-5 * f_rms + 1e-7
+                    d = p2 - ref["pos"]
+                    d -= np.asarray(L) * np.round(d / np.asarray(L))
+                    ev = float(np.sqrt(np.mean((v2 - ref["vel"]) ** 2)))
+                    ex = float(np.sqrt(np.mean(d ** 2)))
+                    segs.append({"step": done, "vel_rms_err": ev, "vel_tol": dv_tol, "pos_rms_err": ex,
+                                 "pos_tol": k * DT * dv_tol + 1e-12, "oracle_s": t_orc,
+                                 "ok": ev <= dv_tol and ex <= k * DT * dv_tol + 1e-12})
+                    done += k
+                s.step(100 - done % 100)
+                done += 100 - done % 100
+                samples.append((done, s.measure()["e_tot_per_atom"]))
+            m = s.measure()
+        finally:
+            s.close()
+        st = np.array([x for x, _ in samples])
+        e = np.array([y for _, y in samples])
+        early = e[(st > 1000) & (st <= 2000)]
+        late = e[st > st[-1] - 1000]
+        # the same measure over each window of `--drift-every` steps
+        windows = []
+        for w0 in range(0, args.drift_steps, args.drift_every):
+            a_ = e[(st > w0) & (st <= w0 + 1000)]
+            b_ = e[(st > w0 + args.drift_every - 1000) & (st <= w0 + args.drift_every)]
+            if a_.size and b_.size:
+                windows.append(float(abs(b_.mean() - a_.mean())))
+        out.append({"workload": wl, "n_atoms": n, "rho": cfg["rho"], "T": cfg["T"], "steps": int(m["step"]),
+                    "window_drift_max_per_atom": max(windows) if windows else None,
+                    "rebuilds": int(m["rebuilds"]), "drift_per_atom": float(abs(late.mean() - early.mean())),
+                    "max_excursion_per_atom": float(np.max(np.abs(e - e[0]))), "e_tot_first": float(e[0]),
+                    "e_tot_last": float(e[-1]), "segments": segs,
+                    "segments_ok": all(x["ok"] for x in segs), "wall_s": time.perf_counter() - t_wall})
+    print(json.dumps({"drift_runs": out, "oracle_threads": oracle.threads(True)}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.drift:
+        drift_runs(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -141,7 +141,10 @@ WORKLOADS = {
     # neighbour list with skin 0.4, reorder every 100 steps
     "wca_fcc64_n1m": dict(n=1048576, rho=0.8, T=1.0, seed=2, skin=0.4, steps=10000),
     # large system, two densities / temperatures
+    # (the pairing of density and temperature is not stated: all four)
     "wca_fcc128_n8m_rho0.6_T0.7": dict(n=8388608, rho=0.6, T=0.7, seed=3, skin=0.4, steps=100000),
+    "wca_fcc128_n8m_rho0.6_T2.0": dict(n=8388608, rho=0.6, T=2.0, seed=3, skin=0.4, steps=100000),
+    "wca_fcc128_n8m_rho1.0_T0.7": dict(n=8388608, rho=1.0, T=0.7, seed=3, skin=0.4, steps=100000),
     "wca_fcc128_n8m_rho1.0_T2.0": dict(n=8388608, rho=1.0, T=2.0, seed=3, skin=0.4, steps=100000),
     # Lennard-Jones system of the paper's comparisons: rho 0.38, T 1.2, shell 0.8
     "lj_fcc64_n1m_rc3": dict(n=1048576, rho=0.38, T=1.2, seed=6, skin=0.8, rc=3.0, steps=6000),
