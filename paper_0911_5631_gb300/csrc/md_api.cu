@@ -241,7 +241,7 @@ struct Sim : SimBase {
     // the neighbour-list build: a block of kWcThreads per x slice of a
     // pencil (a warp per cell), or a thread per cell-ordered atom
     bool warp_build() const { return use_warp_build(prm); }
-    void* build_fn() const { return warp_build() ? kt.build_wc : kt.build; }
+    void* build_fn() const { return warp_build() ? kt.build_wc : (a.list_rows ? kt.build_rows : kt.build); }
     unsigned grid_build() const { return warp_build() ? (unsigned)wc_slices(a) : grid_atoms(); }
     unsigned block_build() const { return warp_build() ? (unsigned)kWcThreads : (unsigned)kBlock; }
 

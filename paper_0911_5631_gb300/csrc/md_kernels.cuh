@@ -291,9 +291,13 @@ __device__ __forceinline__ float from_fix(long long q) {
 // Fixed point with scale 2^32 kept as three int32 partial sums.
 // add(g) adds round(g 2^32) (ties to even) for |g| < 2^30 as
 // a 2^44 + b 2^22 + c with |a| <= 2^18, |b|, |c| <= 2^21: each chunk is
-// rounded to an integer by adding 1.5 2^23 in FP32, and every remainder is
-// exact, so the three sums are exact and independent of the order of the
-// terms, and add(-g) subtracts exactly what add(g) adds.  value()
+// rounded to an integer by the magic-number method -- adding 1.5 2^23 in
+// FP32 round-to-nearest leaves round(x) in the low mantissa bits for
+// |x| < 2^22, so the integer is the bit pattern minus that of 1.5 2^23 (the
+// float-to-integer conversion of C. Hecker, "Let's Get to the (Floating)
+// Point", Game Developer, 1996) -- and every remainder is exact, so the
+// three sums are exact and independent of the order of the terms, and
+// add(-g) subtracts exactly what add(g) adds.  value()
 // assembles the int64 sum.  With at most 512 terms no partial sum leaves
 // int32.  For |g| <= 2^11 the first chunk is zero and its remainder is g
 // itself, so add_small(g) -- the last two chunks alone -- adds exactly
@@ -442,7 +446,6 @@ struct AccMixed {
     // accumulate one interacting pair (r^2 < r_c^2) at separation d
     template <bool kEnergy>
     __device__ __forceinline__ void force(const Args<Mixed>& a, F2 dxy, float dz, float r2) {
-        close |= (r2 < a.close2f);
         float ir2 = __fdividef(1.0f, r2);
         float ir6 = ir2 * ir2 * ir2;
         float fr = 48.0f * ir6 * (ir6 - 0.5f) * ir2;
@@ -452,6 +455,9 @@ struct AccMixed {
             fxy.add_small(gxy);
             fz.add_small(gz);
         } else {
+            // a pair closer than sqrt(close2f) has f/r far above
+            // fix_small_fr, so the close test belongs to this branch only
+            close |= (r2 < a.close2f);
             float gx, gy;
             f2_get(gxy, gx, gy);
             fxy.x.add(gx);
@@ -595,7 +601,7 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int cnt, cons
                 real dz = (qz - pj[k].z) + sh.z;
                 real rr = acc.r2(dx, dy, dz);
                 if (acc.inside(a, rr)) {
-                    if (nq < kQ) queue[nq * kBlock + threadIdx.x] = Queue<P>::make(dx, dy, dz, rr);
+                    if (nq < kQ) queue[nq * blockDim.x + threadIdx.x] = Queue<P>::make(dx, dy, dz, rr);
                     else acc.template force<kEnergy>(a, dx, dy, dz, rr);
                     nq++;
                 }
@@ -604,7 +610,7 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int cnt, cons
     }
     const int nk = min(nq, kQ);
     for (int k = 0; k < nk; k++) {
-        const auto d = queue[k * kBlock + threadIdx.x];
+        const auto d = queue[k * blockDim.x + threadIdx.x];
         acc.template force<kEnergy>(a, d.x, d.y, d.z, d.w);
     }
 }
@@ -1159,14 +1165,14 @@ __device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
 // appended to its list after the m entries already there (they belong to
 // the last shell bin).  A second pass over the 27 cells, run only for an
 // atom that met such a candidate.  Returns the new count.
-template <class P, bool kSort>
+template <class P, bool kSort, bool kRows>
 __device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2* stage, int stride) {
     const float4 ci = a.cand[s];
     const int i = __float_as_int(ci.w);
     int cx, cy, cz;
     unpack_cell(a.cell[i], cx, cy, cz);
-    int* col = a.nbr + list_base(a, i);
-    const int cs = list_stride(a);
+    constexpr int cs = kRows ? 1 : 32;
+    int* col = a.nbr + (kRows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31));
     const int cap = a.cap, n = (int)a.n;
     for (int d = 0; d < 27; d++) {
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
@@ -1192,7 +1198,7 @@ __device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2*
     return m;
 }
 
-template <class P, bool kSort>
+template <class P, bool kSort, bool kRows>
 __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* stage, int stride) {
     Counters* C = a.ctr;
     int m = 0;
@@ -1201,8 +1207,8 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
     const int i = __float_as_int(ci.w);
     int cx, cy, cz;
     unpack_cell(a.cell[i], cx, cy, cz);
-    int* col = a.nbr + list_base(a, i);
-    const int cs = list_stride(a);
+    constexpr int cs = kRows ? 1 : 32;
+    int* col = a.nbr + (kRows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31));
     const int cap = a.cap, n = (int)a.n, self = (int)s;
     const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
     const int xs[3] = {wrap_add(cx, -1, a.G[0]), cx, wrap_add(cx, 1, a.G[0])};
@@ -1246,7 +1252,7 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
             }
         }
     }
-    if (unsure) m = build_band<P, kSort>(a, s, m, stage, stride);
+    if (unsure) m = build_band<P, kSort, kRows>(a, s, m, stage, stride);
     const int kept = m < cap ? m : cap;
     a.nn[i] = kept;
     unsigned long long incl = ~0ull;  // lim byte 255: read all entries
@@ -1290,20 +1296,21 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
     return m;
 }
 
-template <class P>
+template <class P, bool kRows = false>
 __device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* stage, int stride) {
-    return a.shell_bins ? build_item_t<P, true>(a, s, stage, stride) : build_item_t<P, false>(a, s, stage, stride);
+    return a.shell_bins ? build_item_t<P, true, kRows>(a, s, stage, stride)
+                        : build_item_t<P, false, kRows>(a, s, stage, stride);
 }
 
-template <class P>
-__global__ void __launch_bounds__(kBlock) k_build(Args<P> a, int guard) {
+template <class P, bool kRows = false>
+__global__ void __launch_bounds__(kBlock, 4) k_build(Args<P> a, int guard) {
     __shared__ int shm[kBlock / 32];
     __shared__ double shs[kBlock / 32];
     __shared__ int2 s_stage[kBuildStage * kBlock];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     const int64_t s = gtid();
-    const int m = s < a.n ? build_item<P>(a, s, s_stage + threadIdx.x, kBlock) : 0;
+    const int m = s < a.n ? build_item<P, kRows>(a, s, s_stage + threadIdx.x, kBlock) : 0;
     int bm = block_max_int(m, shm);
     double bs = block_sum((double)m, shs);
     if (threadIdx.x == 0) {
@@ -2459,6 +2466,7 @@ KernelTable<P> make_kernel_table() {
     t.gather = (void*)k_gather<P>;
     t.commit = (void*)k_commit<P>;
     t.build = (void*)k_build<P>;
+    t.build_rows = (void*)k_build<P, true>;
     t.build_wc = (void*)k_build_wc<P>;
     t.rebuild_done = (void*)k_rebuild_done<P>;
     t.cond = (void*)k_cond<P>;

@@ -17,6 +17,7 @@ struct KernelTable {
     void* gather;
     void* commit;
     void* build;     // thread per atom
+    void* build_rows;  // the same, lists with each atom's entries contiguous (W transposed)
     void* build_wc;  // warp per home cell (warp-cooperative)
     void* rebuild_done;
     void* cond;
