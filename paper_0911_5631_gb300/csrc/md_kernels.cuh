@@ -403,13 +403,20 @@ __device__ __forceinline__ double drift(double o, double v, double dt) { return 
 
 // Pair coordinate after a drift and the squared displacement in the pair
 // precision (the skin/2 test).
+// kHw: the hardware conversion (on the FP64 pipe) instead of the bit-level
+// one (integer pipe), the same round-to-nearest result.  The grid step
+// kernel, whose integer pipe is its busiest, takes the hardware one; the
+// ensemble engine, whose 1024-thread blocks load the FP64 pipe more, the
+// bit-level one (measured: each choice is the faster one for its kernel).
+template <bool kHw = false>
 __device__ __forceinline__ float moved(float pb, double o, float& p) {
-    // the hardware conversion (on the FP64 pipe): the step kernel is bound
-    // by the integer pipe, which the bit-level conversion would load further
-    float d = __double2float_rn(o);
+    float d;
+    if constexpr (kHw) d = __double2float_rn(o);
+    else d = cvt::f32(o);
     p = pb + d;
     return d * d;
 }
+template <bool kHw = false>
 __device__ __forceinline__ double moved(double pb, double o, double& p) {
     p = __dadd_rn(pb, o);
     return o * o;
@@ -1705,7 +1712,7 @@ __device__ __forceinline__ void stage_wait() {
 // KE/PE/W terms) or the next half kick, the drift into the other pair
 // buffer and the skin/2 test.  Shared by the grid kernel and the
 // per-replica engine.
-template <class P, bool kCells, bool kFinal, bool kLdg = true, bool kRows = false>
+template <class P, bool kCells, bool kFinal, bool kLdg = true, bool kRows = false, bool kHwCvt = false>
 __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, bool active, bool init, bool energy,
                                           int cnt, const int* col, const int* rows, int staged,
                                           const typename P::pos4* __restrict__ pc, typename P::pos4* pn,
@@ -1758,7 +1765,7 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
             oy = drift(oy, vy, a.dt);
             oz = drift(oz, vz, a.dt);
             real px, py, pz;
-            real d2 = moved(pbx, ox, px) + moved(pby, oy, py) + moved(pbz, oz, pz);
+            real d2 = moved<kHwCvt>(pbx, ox, px) + moved<kHwCvt>(pby, oy, py) + moved<kHwCvt>(pbz, oz, pz);
             a.vx[i] = vx; a.vy[i] = vy; a.vz[i] = vz;
             a.ox[i] = ox; a.oy[i] = oy; a.oz[i] = oz;
             pn[i] = make_pos4(px, py, pz, 0);
@@ -1834,8 +1841,8 @@ __global__ void __launch_bounds__(kB, P::kFp64 ? 3 : 5 * kBlock / kB) k_step(Arg
     bool far = false, close = false;
     double ke = 0.0, pe = 0.0, vir = 0.0;
     unsigned d2b = 0u;
-    step_atom<P, kCells, kFinal, kLdg, kRows>(a, i, in, active, init, energy, cnt, col, rows, staged, pc, pn,
-                                              s_shift, s_queue, far, close, ke, pe, vir, d2b);
+    step_atom<P, kCells, kFinal, kLdg, kRows, true>(a, i, in, active, init, energy, cnt, col, rows, staged, pc, pn,
+                                                    s_shift, s_queue, far, close, ke, pe, vir, d2b);
     if (__any_sync(0xffffffffu, far) && (threadIdx.x & 31) == 0) atomicOr(&C->far_flag, 1u);
     if (__any_sync(0xffffffffu, close) && (threadIdx.x & 31) == 0) atomicOr(&C->close_flag, 1);
     warp_max_into(d2b, d2_word(a));  // the running maximum of the squared displacement
