@@ -242,8 +242,10 @@ struct Sim : SimBase {
     // pencil (a warp per cell), or a thread per cell-ordered atom
     bool warp_build() const { return use_warp_build(prm); }
     void* build_fn() const { return warp_build() ? kt.build_wc : (a.list_rows ? kt.build_rows : kt.build); }
-    unsigned grid_build() const { return warp_build() ? (unsigned)wc_slices(a) : grid_atoms(); }
-    unsigned block_build() const { return warp_build() ? (unsigned)kWcThreads : (unsigned)kBlock; }
+    unsigned grid_build() const {
+        return warp_build() ? (unsigned)wc_slices(a) : (unsigned)((a.n + kBuildBlock - 1) / kBuildBlock);
+    }
+    unsigned block_build() const { return warp_build() ? (unsigned)kWcThreads : (unsigned)kBuildBlock; }
 
     // index into kt.step_var of the requested ablation variant, or -1
     int variant_index() const {
@@ -289,13 +291,20 @@ struct Sim : SimBase {
         return MD_OK;
     }
 
-    // The step kernel, then (kStepTailNode) its one-warp closing kernel; the
-    // event `after_step`, when given, is recorded between the two.
+    // The step kernel, then (kStepTailNode) its one-warp closing kernel.
+    // Profiling: the event `after_step` is recorded right after the step
+    // kernel, and then the count of the entries that step read (before the
+    // closing kernel changes the reach), so that the count kernel neither
+    // falls inside the events nor warms the caches for the step.  A step
+    // kernel that closes itself has its entries counted before it.
     int step_kernel_eager(int mode, bool final_node, cudaEvent_t after_step = nullptr) {
         cudaGraphConditionalHandle none = 0;
         int has = 0;
         MD_CUDA(launch(step_fn(final_node), step_grid(final_node), step_block(final_node), a, mode, none, has));
-        if (after_step) MD_CUDA(cudaEventRecord(after_step, stream));
+        if (after_step) {
+            MD_CUDA(cudaEventRecord(after_step, stream));
+            if (kStepTailNode) MD_CUDA(launch(kt.count_reads, grid_atoms(), kBlock, a));
+        }
         if (kStepTailNode) MD_CUDA(launch(tail_fn(final_node), 1, 32, a, mode, none, has));
         return MD_OK;
     }
@@ -444,8 +453,8 @@ struct Sim : SimBase {
                 int r = flag ? rebuild_eager(0) : MD_OK;
                 if (r) return r;
                 if (profiling && flag) MD_CUDA(cudaEventRecord(ev[4 * s + 3], stream));
-                if (profiling) {  // entries the step will read, outside its events
-                    MD_CUDA(launch(kt.count_reads, grid_atoms(), kBlock, a));
+                if (profiling) {  // (the step closes itself: count before it)
+                    if (!kStepTailNode) MD_CUDA(launch(kt.count_reads, grid_atoms(), kBlock, a));
                     MD_CUDA(cudaEventRecord(ev[4 * s], stream));
                 }
                 r = step_kernel_eager(kModeAuto, s + 1 == nsteps, profiling ? ev[4 * s + 1] : nullptr);

@@ -27,9 +27,18 @@ constexpr int kStageRows = 12;  // neighbour-list rows a step-kernel warp copies
 // distance at the build and records, for k = 1 .. kShellBins, how many
 // entries lie below r_c + k skin / kShellBins; a step then reads only the
 // entries that the displacements since the build can have brought inside
-// r_c.  The build sorts up to kBuildStage entries per atom in shared memory.
+// r_c.  The build stages up to kBuildStage candidates per atom in shared
+// memory.
 constexpr int kShellBins = 8;
-constexpr int kBuildStage = 16;
+constexpr int kBuildStage = 20;
+// Threads per block of the thread-per-atom build (its stage: kBuildStage
+// 8-byte words per thread in shared memory; 20 measured best at the 1M-atom
+// workload, against 16, 24 and 32).
+constexpr int kBuildBlock = 128;
+// The build's candidate loop issues kBuildUnroll loads before it uses them,
+// and the cell ranges of the next (c_y, c_z) row are loaded while a row runs.
+constexpr int kBuildUnroll = 4;
+constexpr bool kBuildPrefetch = true;
 // The grid kernels keep the running maximum of the squared displacement in
 // kD2Buckets words, one per 128-byte line (block b uses word b mod
 // kD2Buckets), so that the atomics of the many warps of a launch do not
@@ -37,7 +46,12 @@ constexpr int kBuildStage = 16;
 constexpr int kD2Buckets = 64;
 // Dynamic shared memory of the ensemble engine, ints per thread: the larger
 // of the step's staged rows and the build's staging (entries and distances).
-constexpr int kEnsSmemInts = kStageRows > 2 * kBuildStage ? kStageRows : 2 * kBuildStage;
+// The engine's build stages kEnsBuildStage candidates per atom: a deeper
+// stage leaves its 1024-thread blocks less L1 for the step phase, a shallower
+// one sends too many atoms of its denser replicas to the rescan (measured
+// at the 512-replica workload: 16 beats 12, 14, 20 and 24).
+constexpr int kEnsBuildStage = 16;
+constexpr int kEnsSmemInts = kStageRows > 2 * kEnsBuildStage ? kStageRows : 2 * kEnsBuildStage;
 // Elements per block of the cell-count scan (kBlock threads x 8).
 constexpr int kScanTile = 2048;
 // Largest neighbour capacity of the mixed form (its fixed-point partial

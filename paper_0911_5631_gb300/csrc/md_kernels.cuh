@@ -1154,26 +1154,27 @@ __device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
 // the 27 cells around its cell and record every j != i with r < r_n in its
 // column together with the cell-offset code.  The decision is the exact
 // FP64 criterion: FP32 coordinates settle every candidate outside a narrow
-// band around r_n^2, the FP64 test the rest (in build_band, after the scan,
-// so that the rare FP64 path costs the scan loop no registers).  The three cells of one
-// (c_y, c_z) row sit at base + c_x * stride in the pencil order, so each row
-// costs one index computation and the six range bounds are read together.
+// band [rn2_lo, rn2_hi) around r_n^2, the FP64 test the rest.  The three
+// cells of one (c_y, c_z) row sit at base + c_x * stride in the pencil
+// order, so each row costs one index computation and the six range bounds
+// are read together.
 //
-// The first kBuildStage entries wait in shared memory, each with its
-// squared distance, in one 8-byte word stage[t * stride] private to the
-// thread.  A warp runs the candidate loop's accepting code whenever any of
-// its lanes accepts, so that code is only a predicated store; afterwards the
-// entries are written out ordered by shell bin (a counting sort whose bin
-// counts sit in the bytes of one 64-bit word) and lim receives the number
-// of entries below each bin boundary.  An atom with more entries keeps its
-// order of discovery and a lim of "all entries".
-// The candidates of the atom in cell-ordered slot s whose FP32 distance lies
-// in the band around r_n^2, decided by the exact FP64 criterion and
-// appended to its list after the m entries already there (they belong to
-// the last shell bin).  A second pass over the 27 cells, run only for an
-// atom that met such a candidate.  Returns the new count.
-template <class P, bool kSort, bool kRows>
-__device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2* stage, int stride) {
+// The scan loop only stages: every candidate with FP32 r^2 below rn2_hi is
+// written, with its squared distance, to the thread's next 8-byte word
+// stage[m * stride] in shared memory (a rejected candidate's word is
+// overwritten by the next one), so that a candidate costs its distance, one
+// store and no branch.  The loop issues kBuildUnroll candidate loads before
+// it uses them (loads past a cell's end are predicated off) and loads the
+// next row's cell ranges while a row runs: the loop is bound by the latency
+// of those L1 hits, not by its instructions.  Afterwards the staged band
+// entries get the FP64 test (rare), the survivors are written out ordered
+// by shell bin (a counting sort whose bin counts sit in the bytes of one
+// 64-bit word) and lim receives the number of entries below each bin
+// boundary.  An atom with more than K (the stage depth) staged candidates
+// is scanned again by build_all, which writes its entries in order of
+// discovery with a lim of "all entries".
+template <class P, bool kRows>
+__device__ __noinline__ int build_all(const Args<P>& a, int64_t s) {
     const float4 ci = a.cand[s];
     const int i = __float_as_int(ci.w);
     int cx, cy, cz;
@@ -1181,6 +1182,7 @@ __device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2*
     constexpr int cs = kRows ? 1 : 32;
     int* col = a.nbr + (kRows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31));
     const int cap = a.cap, n = (int)a.n;
+    int m = 0;
     for (int d = 0; d < 27; d++) {
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
         const int c = cell_index(wrap_add(cx, dx, a.G[0]), wrap_add(cy, dy, a.G[1]), wrap_add(cz, dz, a.G[2]), a.G);
@@ -1193,23 +1195,20 @@ __device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m, int2*
             const float ey = (ci.y - (float)dy * a.wf[1]) - pj.y;
             const float ez = (ci.z - (float)dz * a.wf[2]) - pj.z;
             const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            if (!(rr >= a.rn2_lo && rr < a.rn2_hi)) continue;
+            if (!(rr < a.rn2_hi)) continue;
             const int j = __float_as_int(pj.w);
-            if (!within_rn_fp64(a, i, j, code)) continue;
-            const int e = j | (int)(code << kCodeShift);
-            if (kSort && m < kBuildStage) stage[m * stride] = make_int2(e, __float_as_int(rr));
-            else if (m < cap) col[(size_t)m * cs] = e;
+            if (!(rr < a.rn2_lo) && !within_rn_fp64(a, i, j, code)) continue;
+            if (m < cap) col[(size_t)m * cs] = j | (int)(code << kCodeShift);
             m++;
         }
     }
     return m;
 }
 
-template <class P, bool kSort, bool kRows>
+template <class P, bool kSort, bool kRows, int K>
 __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* stage, int stride) {
     Counters* C = a.ctr;
-    int m = 0;
-    bool unsure = false;  // a candidate in the band around r_n^2 was met
+    int m = 0;  // staged candidates (FP32 r^2 < rn2_hi)
     const float4 ci = a.cand[s];
     const int i = __float_as_int(ci.w);
     int cx, cy, cz;
@@ -1217,84 +1216,109 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
     constexpr int cs = kRows ? 1 : 32;
     int* col = a.nbr + (kRows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31));
     const int cap = a.cap, n = (int)a.n, self = (int)s;
-    const float lo2 = a.rn2_lo, hi2 = a.rn2_hi;
+    const float hi2 = a.rn2_hi;
     const int xs[3] = {wrap_add(cx, -1, a.G[0]), cx, wrap_add(cx, 1, a.G[0])};
     const float qxs[3] = {ci.x + a.wf[0], ci.x, ci.x - a.wf[0]};  // x seen from cells x-1, x, x+1
-    for (int dz = -1; dz <= 1; dz++) {
-        const int z = wrap_add(cz, dz, a.G[2]);
+    // candidate ranges of the three cells of row r = (d_y + 1) + 3 (d_z + 1)
+    auto row_bounds = [&](int r, int lo[3], int hi[3]) {
+        const int y = wrap_add(cy, r % 3 - 1, a.G[1]), z = wrap_add(cz, r / 3 - 1, a.G[2]);
+        const PencilRow pr = pencil_row(y, z, a.G);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const int c = pr.base + xs[k] * pr.stride;
+            lo[k] = a.cell_start[c];
+            hi[k] = min(a.cell_start[c + 1], n);
+        }
+    };
+    int lo[3], hi[3];
+    row_bounds(0, lo, hi);
+#pragma unroll 1
+    for (int r = 0; r < 9; r++) {
+        int nlo[3], nhi[3];  // the next row's bounds, loaded while this row runs
+        if (kBuildPrefetch) row_bounds(r < 8 ? r + 1 : r, nlo, nhi);
+        const int dy = r % 3 - 1, dz = r / 3 - 1;
         const float qz = ci.z - (float)dz * a.wf[2];
-        for (int dy = -1; dy <= 1; dy++) {
-            const int y = wrap_add(cy, dy, a.G[1]);
-            const float qy = ci.y - (float)dy * a.wf[1];
-            const unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
-            const PencilRow pr = pencil_row(y, z, a.G);
-            int lo[3], hi[3];
+        const float qy = ci.y - (float)dy * a.wf[1];
+        const unsigned code_yz = ((unsigned)(dy + 1) << 2) | ((unsigned)(dz + 1) << 4);
+        auto stage_one = [&](const float4& pj, float qx, int code, int t) {
+            const float ex = qx - pj.x;
+            const float ey = qy - pj.y;
+            const float ez = qz - pj.z;
+            const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (m < K) stage[m * stride] = make_int2(__float_as_int(pj.w) | code, __float_as_int(rr));
+            m += (rr < hi2 && t != self) ? 1 : 0;
+        };
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const int c = pr.base + xs[k] * pr.stride;
-                lo[k] = a.cell_start[c];
-                hi[k] = min(a.cell_start[c + 1], n);
-            }
+        for (int k = 0; k < 3; k++) {
+            const float qx = qxs[k];
+            const int code = (int)(((unsigned)k | code_yz) << kCodeShift);
+            const int end = hi[k];
+            for (int t = lo[k]; t < end; t += kBuildUnroll) {
+                float4 pj[kBuildUnroll];  // all loads first
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const float qx = qxs[k];
-                const int code = (int)(((unsigned)k | code_yz) << kCodeShift);
-                for (int t = lo[k]; t < hi[k]; t++) {
-                    const float4 pj = __ldg(a.cand + t);
-                    const float ex = qx - pj.x;
-                    const float ey = qy - pj.y;
-                    const float ez = qz - pj.z;
-                    const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                    const int j = __float_as_int(pj.w);
-                    bool take = rr < lo2 && t != self;
-                    unsure |= !(rr < lo2) && rr < hi2 && t != self;
-                    if constexpr (kSort) {
-                        if (take && m < kBuildStage) stage[m * stride] = make_int2(j | code, __float_as_int(rr));
-                        if (take && m >= kBuildStage && m < cap) col[(size_t)m * cs] = j | code;
-                    } else {
-                        if (take && m < cap) col[(size_t)m * cs] = j | code;
-                    }
-                    m += take ? 1 : 0;
-                }
+                for (int u = 0; u < kBuildUnroll; u++)
+                    pj[u] = (u == 0 || t + u < end) ? __ldg(a.cand + t + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int u = 0; u < kBuildUnroll; u++)
+                    if (u == 0 || t + u < end) stage_one(pj[u], qx, code, t + u);
             }
         }
+        if (kBuildPrefetch) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) { lo[k] = nlo[k]; hi[k] = nhi[k]; }
+        } else if (r < 8) {
+            row_bounds(r + 1, lo, hi);
+        }
     }
-    if (unsure) m = build_band<P, kSort, kRows>(a, s, m, stage, stride);
-    const int kept = m < cap ? m : cap;
-    a.nn[i] = kept;
-    unsigned long long incl = ~0ull;  // lim byte 255: read all entries
-    if (kSort && m <= kBuildStage && m <= cap) {
-        unsigned hlo = 0u, hhi = 0u;  // entries of shell bin b in byte b of (hhi:hlo)
+    if (m > K) {  // rare: too long for the stage
+        m = build_all<P, kRows>(a, s);
+        const int kept = m < cap ? m : cap;
+        a.nn[i] = kept;
+        if constexpr (kSort) {
+#pragma unroll
+            for (int k = 1; k < kShellBins; k++) a.lim[(size_t)(k - 1) * a.n + i] = 255;
+        }
+    } else {
+        // FP64 test of the band entries; bin of each survivor (kShellBins
+        // marks a rejected one) and the bin counts in the bytes of (hhi:hlo)
+        const float lo2 = a.rn2_lo;
+        unsigned hlo = 0u, hhi = 0u;
+        int kept = 0;
         for (int t = 0; t < m; t++) {
-            const int b = shell_bin(a, __int_as_float(stage[t * stride].y));
+            const int2 e = stage[t * stride];
+            const float rr = __int_as_float(e.y);
+            bool keep = true;
+            if (!(rr < lo2)) keep = within_rn_fp64(a, i, e.x & kIndexMask, (unsigned)e.x >> kCodeShift);
+            const int b = !keep ? kShellBins : (kSort ? shell_bin(a, rr) : 0);
             stage[t * stride].y = b;
-            const unsigned inc = 1u << (8 * (b & 3));
+            kept += keep ? 1 : 0;
+            const unsigned inc = keep ? 1u << (8 * (b & 3)) : 0u;
             hlo += b < 4 ? inc : 0u;
             hhi += b < 4 ? 0u : inc;
         }
         // byte b of incl: entries of bins 0..b, i.e. those below the
-        // boundary r_c + (b + 1) skin / kShellBins (no byte exceeds kBuildStage)
-        incl = (((unsigned long long)hhi << 32) | hlo) * 0x0101010101010101ull;
+        // boundary r_c + (b + 1) skin / kShellBins (no byte exceeds K)
+        const unsigned long long incl = (((unsigned long long)hhi << 32) | hlo) * 0x0101010101010101ull;
         const unsigned long long first = incl << 8;  // exclusive: first slot of each bin
         unsigned nlo = (unsigned)first, nhi = (unsigned)(first >> 32);
         for (int t = 0; t < m; t++) {
             const int2 e = stage[t * stride];
             const int b = e.y;
+            if (b == kShellBins) continue;
             const int sh = 8 * (b & 3);
             const int dst = (int)(((b < 4 ? nlo : nhi) >> sh) & 0xffu);
             const unsigned inc = 1u << sh;
             nlo += b < 4 ? inc : 0u;
             nhi += b < 4 ? 0u : inc;
-            col[(size_t)dst * cs] = e.x;
+            if (dst < cap) col[(size_t)dst * cs] = e.x;
         }
-    } else if (kSort) {
-        const int ns = min(kept, kBuildStage);
-        for (int t = 0; t < ns; t++) col[(size_t)t * cs] = stage[t * stride].x;
-    }
-    if constexpr (kSort) {
+        a.nn[i] = kept < cap ? kept : cap;
+        if constexpr (kSort) {
 #pragma unroll
-        for (int k = 1; k < kShellBins; k++)
-            a.lim[(size_t)(k - 1) * a.n + i] = (unsigned char)(incl >> (8 * (k - 1)));
+            for (int k = 1; k < kShellBins; k++)
+                a.lim[(size_t)(k - 1) * a.n + i] = (unsigned char)(incl >> (8 * (k - 1)));
+        }
+        m = kept;
     }
     if (m > cap) {
         atomicOr(&C->error, kErrOverflow);
@@ -1303,24 +1327,39 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
     return m;
 }
 
-template <class P, bool kRows = false>
+// K: the stage depth (8-byte words per thread at stage[t * stride]).
+template <class P, bool kRows = false, int K = kBuildStage>
 __device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* stage, int stride) {
-    return a.shell_bins ? build_item_t<P, true, kRows>(a, s, stage, stride)
-                        : build_item_t<P, false, kRows>(a, s, stage, stride);
+    return a.shell_bins ? build_item_t<P, true, kRows, K>(a, s, stage, stride)
+                        : build_item_t<P, false, kRows, K>(a, s, stage, stride);
 }
 
 template <class P, bool kRows = false>
-__global__ void __launch_bounds__(kBlock, 4) k_build(Args<P> a, int guard) {
-    __shared__ int shm[kBlock / 32];
-    __shared__ double shs[kBlock / 32];
-    __shared__ int2 s_stage[kBuildStage * kBlock];
+__global__ void __launch_bounds__(kBuildBlock, 8) k_build(Args<P> a, int guard) {
+    constexpr int kWarps = kBuildBlock / 32;
+    __shared__ int s_max[kWarps], s_sum[kWarps];
+    __shared__ int2 s_stage[kBuildStage * kBuildBlock];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     const int64_t s = gtid();
-    const int m = s < a.n ? build_item<P, kRows>(a, s, s_stage + threadIdx.x, kBlock) : 0;
-    int bm = block_max_int(m, shm);
-    double bs = block_sum((double)m, shs);
+    const int m = s < a.n ? build_item<P, kRows>(a, s, s_stage + threadIdx.x, kBuildBlock) : 0;
+    // block maximum and sum of the list lengths (m <= 512, so the block's
+    // sum fits an int)
+    int bm = m, bs = m;
+    for (int o = 16; o > 0; o >>= 1) {
+        bm = max(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+        bs += __shfl_xor_sync(0xffffffffu, bs, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        s_max[threadIdx.x >> 5] = bm;
+        s_sum[threadIdx.x >> 5] = bs;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        for (int w = 1; w < kWarps; w++) {
+            bm = max(bm, s_max[w]);
+            bs += s_sum[w];
+        }
         atomicMax(&C->max_nn, bm);
         atomicAdd((unsigned long long*)&C->list_entries, (unsigned long long)bs);
     }
@@ -2191,7 +2230,7 @@ __device__ __noinline__ void ens_scan(const Args<P>& a, EnsShared& sh) {
 
 // The rebuild branch of one replica (the kernels k_bin .. k_rebuild_done,
 // with team barriers between the phases).  stage: the block's dynamic
-// shared memory, kBuildStage 8-byte words per thread for the build.
+// shared memory, kEnsBuildStage 8-byte words per thread for the build.
 template <class P>
 __device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh, int* stage, Team tm) {
     Counters* C = a.ctr;
@@ -2214,7 +2253,8 @@ __device__ __noinline__ void ens_rebuild(const Args<P>& a, EnsShared& sh, int* s
     int mx = 0;
     long long sum = 0;
     for (int64_t s = t0; s < n; s += dt) {
-        const int m = build_item<P>(a, s, reinterpret_cast<int2*>(stage) + threadIdx.x, (int)blockDim.x);
+        const int m = build_item<P, false, kEnsBuildStage>(a, s, reinterpret_cast<int2*>(stage) + threadIdx.x,
+                                                           (int)blockDim.x);
         mx = max(mx, m);
         sum += m;
     }
