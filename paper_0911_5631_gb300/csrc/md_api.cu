@@ -183,7 +183,7 @@ struct Sim : SimBase {
         chk(alloc(&a.ox, n)); chk(alloc(&a.oy, n)); chk(alloc(&a.oz, n));
         chk(alloc(&a.vx, n)); chk(alloc(&a.vy, n)); chk(alloc(&a.vz, n));
         chk(alloc(&a.fx, n)); chk(alloc(&a.fy, n)); chk(alloc(&a.fz, n));
-        chk(alloc(&a.pA, n)); chk(alloc(&a.pB, n)); chk(alloc(&a.cand, n));
+        chk(alloc(&a.pA, pair_slots(n))); chk(alloc(&a.pB, pair_slots(n))); chk(alloc(&a.cand, n));
         chk(alloc(&a.s_cell, n)); chk(alloc(&a.s_perm, n));
         chk(alloc(&a.s_pbx, n)); chk(alloc(&a.s_pby, n)); chk(alloc(&a.s_pbz, n));
         chk(alloc(&a.s_ox, n)); chk(alloc(&a.s_oy, n)); chk(alloc(&a.s_oz, n));
@@ -199,6 +199,7 @@ struct Sim : SimBase {
         r = alloc_nbr(a.cap);
         if (r) return r;
         MD_CUDA(cudaMemsetAsync(a.count, 0, sizeof(int) * a.ncells, stream));
+        MD_CUDA(cudaMemsetAsync(a.tile_sum, 0, sizeof(int) * a.ntiles, stream));
         MD_CUDA(cudaMemsetAsync(a.ctr, 0, sizeof(Counters), stream));
         MD_CUDA(cudaMemsetAsync(a.d2b, 0, sizeof(unsigned) * kD2Buckets * 32, stream));
         MD_CUDA(cudaMemsetAsync(a.nn, 0, sizeof(int) * n, stream));
@@ -279,8 +280,6 @@ struct Sim : SimBase {
     // at once unless the device rebuild flag is set.
     int rebuild_eager(int g = 1) {
         MD_CUDA(launch(kt.bin, grid_atoms(), kBlock, a, g));
-        MD_CUDA(launch(kt.scan_tiles, (unsigned)a.ntiles, kBlock, a, g));
-        MD_CUDA(launch(kt.scan_top, 1, 1024, a, g));
         MD_CUDA(launch(kt.scan_apply, (unsigned)a.ntiles, kBlock, a, g));
         MD_CUDA(launch(kt.scatter, grid_scatter(), kBlock, a, g));
         MD_CUDA(launch(kt.cellsort, grid_cells(), kBlock, a, g));
@@ -346,8 +345,6 @@ struct Sim : SimBase {
             return e;
         };
         MD_CUDA(chain(add_kernel(body, nullptr, &cur, kt.bin, grid_atoms(), kBlock, a, g)));
-        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scan_tiles, (unsigned)a.ntiles, kBlock, a, g)));
-        MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scan_top, 1, 1024, a, g)));
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scan_apply, (unsigned)a.ntiles, kBlock, a, g)));
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.scatter, grid_scatter(), kBlock, a, g)));
         MD_CUDA(chain(add_kernel(body, &prev, &cur, kt.cellsort, grid_cells(), kBlock, a, g)));
@@ -789,7 +786,7 @@ struct Sim : SimBase {
         if (r) return r;
         std::memset(out, 0, sizeof(*out));
         // every rebuild branch that ran launched its kernels
-        int per_rebuild = prm.cell_list_only ? 9 : 10;
+        int per_rebuild = prm.cell_list_only ? 7 : 8;
         int64_t body = prm.use_graphs && !profiling ? (int64_t)c.rebuilds * per_rebuild : 0;
         out->launches = launches + body;
         out->step_kernel_launches = step_launches;

@@ -155,7 +155,8 @@ struct alignas(16) Args {
     double w[3];        // cell widths
     double hw[3];       // half cell widths
     float hwf_in[3];    // FP32 bound below which an offset is surely inside its cell
-    float pad1;
+    unsigned jmask;     // pair_slots(n) - 1: masks a list entry to its index (below n for every
+                        // entry a build writes) and keeps any masked index inside pA / pB
     double hw_in[3];    // FP64 bound below which the whole-cell moves of a re-binning are exact
     float wf[3];
     double dt, h;       // time step and half step
@@ -183,7 +184,7 @@ struct alignas(16) Args {
     double* ox; double* oy; double* oz; // displacement since the last build
     vel* vx; vel* vy; vel* vz;
     real* fx; real* fy; real* fz;      // forces of the last completed step
-    pos4* pA; pos4* pB;                // current cell-relative coordinates (ping-pong)
+    pos4* pA; pos4* pB;                // current cell-relative coordinates (ping-pong), pair_slots(n) each
     float4* cand;                      // FP32 coordinates in cell order + storage index
 
     // reorder scratch (same shapes as the state)
@@ -212,6 +213,17 @@ struct alignas(16) Args {
     double* io_pos;     // [3 n] staging for set/get (user order, AoS)
     double* io_vel;     // [3 n]
 };
+
+// Slots of each pair-coordinate buffer: n rounded up to a power of two, so
+// that the force loop's gather index, an entry masked with jmask =
+// pair_slots(n) - 1, stays inside the buffer whatever the entry holds (a
+// clamp to n - 1 would cost the loop one more integer instruction per
+// entry).  No entry a build writes has an index of n or more.
+__host__ __device__ __forceinline__ int64_t pair_slots(int64_t n) {
+    int64_t s = 1;
+    while (s < n) s <<= 1;
+    return s;
+}
 
 // Entry m of atom i's neighbour list (Sec. 3.4, W_{m,i}) sits at
 // list_base(i) + m list_stride: by default the columns of a warp's 32 atoms

@@ -122,7 +122,7 @@ int64_t lay_out(A& a, const md_plan_t& plan, char* base) {
     at(a.ox, n); at(a.oy, n); at(a.oz, n);
     at(a.vx, n); at(a.vy, n); at(a.vz, n);
     at(a.fx, n); at(a.fy, n); at(a.fz, n);
-    at(a.pA, n); at(a.pB, n); at(a.cand, n);
+    at(a.pA, pair_slots(n)); at(a.pB, pair_slots(n)); at(a.cand, n);
     at(a.s_cell, n); at(a.s_perm, n);
     at(a.s_pbx, n); at(a.s_pby, n); at(a.s_pbz, n);
     at(a.s_ox, n); at(a.s_oy, n); at(a.s_oz, n);

@@ -90,7 +90,7 @@ inline int resolve_plan(const double box[3], int64_t n, double rc, double skin, 
                        3 * real_b /*scratch*/ +
                        4 /*order*/ + 4 /*nn*/ + (kShellBins - 1) /*lim*/ + 48 /*io*/;
     int64_t ncol = (n + 31) / 32 * 32;
-    out->device_bytes = per_atom * n + ncol * cap * 4 + (2 * nc + 1) * 4 + ((nc + kScanTile - 1) / kScanTile) * 4 +
+    out->device_bytes = per_atom * n + 2 * pos4_b * (pair_slots(n) - n) + ncol * cap * 4 + (2 * nc + 1) * 4 + ((nc + kScanTile - 1) / kScanTile) * 4 +
                         3 * nb * 8 + (int64_t)sizeof(Counters) + kD2Buckets * 32 * 4;
     return MD_OK;
 }
@@ -106,6 +106,7 @@ template <class P>
 void fill_args_scalars(Args<P>& a, const md_plan_t& plan, const double box[3], int64_t n, double rc, double skin,
                        double dt, int cell_list_only, int reorder_interval, int shell_bins = 1) {
     a.n = n;
+    a.jmask = (unsigned)(pair_slots(n) - 1);
     a.cap = plan.nbr_capacity;
     a.ncells = (int)plan.n_cells;
     for (int k = 0; k < 3; k++) {

@@ -586,7 +586,7 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int cnt, cons
     using real = typename P::real;
     using pos4 = typename P::pos4;
     constexpr int kQ = Queue<P>::kSlots;
-    const unsigned nlast = (unsigned)(a.n - 1);  // entries are always < n; the clamp only guards memory
+    const unsigned jmask = a.jmask;  // entries are always < n; the mask only guards memory
     int nq = 0;
     for (int m = 0; m < cnt; m += 4) {
         unsigned e[4];
@@ -598,7 +598,7 @@ __device__ __forceinline__ void forces_from_list(const Args<P>& a, int cnt, cons
                                  : 0u;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (m + k < cnt) pj[k] = ld_pos4(pc + min(e[k] & (unsigned)kIndexMask, nlast));
+            if (m + k < cnt) pj[k] = ld_pos4(pc + (e[k] & jmask));
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (m + k < cnt) {
@@ -651,7 +651,7 @@ template <bool kEnergy, bool kLdg = true, bool kRows = false>
 __device__ __forceinline__ void forces_mixed(const Args<Mixed>& a, int cnt, const int* col, const int* rows,
                                              int staged, float qx, float qy, float qz,
                                              const float4* __restrict__ pc, AccMixed& acc) {
-    const unsigned nlast = (unsigned)(a.n - 1);  // entries are always < n; the clamp only guards memory
+    const unsigned jmask = a.jmask;  // entries are always < n; the mask only guards memory
     const int lane = threadIdx.x & 31;
     const F2 qxy = f2(qx, qy);
     const F2 wxy = f2(a.wf[0], a.wf[1]);
@@ -679,7 +679,7 @@ __device__ __forceinline__ void forces_mixed(const Args<Mixed>& a, int cnt, cons
         for (int k = 0; k < 4; k++) e[k] = (unsigned)rows[(m + k) * 32 + lane];  // rows past ns are unused
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (m + k < ns) pj[k] = gather4<kLdg>(pc + min(e[k] & (unsigned)kIndexMask, nlast));
+            if (m + k < ns) pj[k] = gather4<kLdg>(pc + (e[k] & jmask));
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (m + k < ns) pair(e[k], pj[k]);
@@ -692,7 +692,7 @@ __device__ __forceinline__ void forces_mixed(const Args<Mixed>& a, int cnt, cons
         for (int k = 0; k < 4; k++) e[k] = (m + k < cnt) ? (unsigned)__ldcs(col + (size_t)(m + k) * kStride) : 0u;
 #pragma unroll
         for (int k = 0; k < 4; k++)
-            if (m + k < cnt) pj[k] = gather4<kLdg>(pc + min(e[k] & (unsigned)kIndexMask, nlast));
+            if (m + k < cnt) pj[k] = gather4<kLdg>(pc + (e[k] & jmask));
 #pragma unroll
         for (int k = 0; k < 4; k++)
             if (m + k < cnt) pair(e[k], pj[k]);
@@ -826,7 +826,7 @@ __global__ void k_clear_overflow(Counters* C) {
 // operation on the cell coordinate).  Refreshes the pair coordinate and
 // counts the atoms of each cell.
 template <class P>
-__device__ __forceinline__ void bin_item(const Args<P>& a, int64_t i) {
+__device__ __forceinline__ int bin_item(const Args<P>& a, int64_t i) {
     using real = typename P::real;
     Counters* C = a.ctr;
     int cc[3];
@@ -865,85 +865,46 @@ __device__ __forceinline__ void bin_item(const Args<P>& a, int64_t i) {
     a.cell[i] = pack_cell(cc[0], cc[1], cc[2]);
     typename P::pos4* pc = C->parity ? a.pB : a.pA;
     pc[i] = make_pos4(pair_coord(pb[0], o[0]), pair_coord(pb[1], o[1]), pair_coord(pb[2], o[2]), 0);
-    a.rank[i] = atomicAdd(&a.count[cell_index(cc[0], cc[1], cc[2], a.G)], 1);
+    const int c = cell_index(cc[0], cc[1], cc[2], a.G);
+    a.rank[i] = atomicAdd(&a.count[c], 1);
+    return c;
 }
 
+// Binning of every atom, and phase 1 of the exclusive scan of the cell
+// counts: the atoms of each scan tile (kScanTile consecutive cells) are
+// added to its total, one atomic per tile present in a warp (a warp's atoms
+// are mostly in one tile).  Also resets the per-build maxima.
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_bin(Args<P> a, int guard) {
-    using real = typename P::real;
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
-    int64_t i = gtid();
-    if (i >= a.n) return;
-    bin_item<P>(a, i);
-}
-
-// Exclusive scan of the cell counts, phase 1: per-tile totals.
-template <class P>
-__global__ void __launch_bounds__(kBlock) k_scan_tiles(Args<P> a, int guard) {
-    __shared__ double sh[kBlock / 32];
-    if (guard && !a.ctr->rebuild_flag) return;
-    int base = blockIdx.x * kScanTile;
-    long long s = 0;
-    for (int k = 0; k < kScanTile / kBlock; k++) {
-        int c = base + k * kBlock + threadIdx.x;
-        if (c < a.ncells) s += a.count[c];
-    }
-    double t = block_sum((double)s, sh);  // exact: counts are small integers
-    if (threadIdx.x == 0) a.tile_sum[blockIdx.x] = (int)t;
-}
-
-// Phase 2: one block turns tile totals into exclusive tile offsets.  Also
-// resets the per-build maxima.
-template <class P>
-__global__ void __launch_bounds__(1024) k_scan_top(Args<P> a, int guard) {
-    __shared__ int warp_tot[32];
-    __shared__ int carry;
-    Counters* C = a.ctr;
-    if (guard && !C->rebuild_flag) return;
-    if (threadIdx.x == 0) {
-        carry = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         C->max_occ = 0;
         C->max_nn = 0;
         C->list_entries = 0;
     }
-    __syncthreads();
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < a.ntiles; base += 1024) {
-        int idx = base + threadIdx.x;
-        int v = idx < a.ntiles ? a.tile_sum[idx] : 0;
-        int x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) warp_tot[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int t = warp_tot[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            warp_tot[lane] = t;  // inclusive over warps
-        }
-        __syncthreads();
-        int excl = x - v + (warp > 0 ? warp_tot[warp - 1] : 0) + carry;
-        if (idx < a.ntiles) a.tile_sum[idx] = excl;
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + v;
-        __syncthreads();
-    }
+    const int64_t i = gtid();
+    const int tile = i < a.n ? bin_item<P>(a, i) / kScanTile : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, tile);
+    if (tile >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&a.tile_sum[tile], __popc(peers));
 }
 
-// Phase 3: each tile scans its counts from its offset into cell_start and
-// records the largest occupancy (the paper's layer count N_l).
+// Phase 2: each tile adds up the totals of the tiles below it (its offset),
+// scans its counts from there into cell_start and records the largest
+// occupancy (the paper's layer count N_l).
 template <class P>
 __global__ void __launch_bounds__(kBlock) k_scan_apply(Args<P> a, int guard) {
     __shared__ int warp_tot[kBlock / 32];
     __shared__ int shm[kBlock / 32];
+    __shared__ int s_pre[kBlock / 32];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
+    {
+        int pre = 0;
+        for (int t = threadIdx.x; t < (int)blockIdx.x; t += kBlock) pre += a.tile_sum[t];
+        for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+        if ((threadIdx.x & 31) == 0) s_pre[threadIdx.x >> 5] = pre;
+    }
     constexpr int E = kScanTile / kBlock;  // 8 per thread
     int base = blockIdx.x * kScanTile + threadIdx.x * E;
     int v[E];
@@ -964,7 +925,8 @@ __global__ void __launch_bounds__(kBlock) k_scan_apply(Args<P> a, int guard) {
     __syncthreads();
     int before = 0;
     for (int k = 0; k < warp; k++) before += warp_tot[k];
-    int run = a.tile_sum[blockIdx.x] + before + x - tot;
+    for (int k = 0; k < kBlock / 32; k++) before += s_pre[k];
+    int run = before + x - tot;
 #pragma unroll
     for (int k = 0; k < E; k++) {
         if (base + k < a.ncells) a.cell_start[base + k] = run;
@@ -988,8 +950,9 @@ template <class P>
 __global__ void __launch_bounds__(kBlock) k_scatter(Args<P> a, int guard) {
     if (guard && !a.ctr->rebuild_flag) return;
     for (int64_t t = gtid(); t < a.n; t += (int64_t)gridDim.x * blockDim.x) scatter_item<P>(a, t);
-    // counts are no longer needed once cell_start is known
+    // counts and tile totals are no longer needed once cell_start is known
     for (int64_t t = gtid(); t < a.ncells; t += (int64_t)gridDim.x * blockDim.x) a.count[t] = 0;
+    for (int64_t t = gtid(); t < a.ntiles; t += (int64_t)gridDim.x * blockDim.x) a.tile_sum[t] = 0;
 }
 
 // Makes the order inside each cell deterministic (ascending storage index).
@@ -1815,10 +1778,31 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
     }
 }
 
+// The counters a step's closing work reads, loaded by lane 0 in one round
+// trip to L2 (other blocks of the step wrote the flags: read past L1).
+struct CloseIn {
+    int err = 0, par = 0, close = 0;
+    unsigned far = 0u;
+    long long left = 0, step = 0, since = 0;
+};
+__device__ __forceinline__ CloseIn read_close_in(const Counters* C) {
+    CloseIn r;
+    if ((threadIdx.x & 31) == 0) {
+        r.err = __ldcg(&C->error);
+        r.par = __ldcg(&C->parity);
+        r.close = __ldcg(&C->close_flag);
+        r.far = __ldcg(&C->far_flag);
+        r.left = __ldcg(&C->steps_left);
+        r.step = __ldcg(&C->step);
+        r.since = __ldcg(&C->since_reorder);
+    }
+    return r;
+}
+
 template <class P>
-__device__ __forceinline__ void close_step(const Args<P>& a, int err, long long left, int par, bool init, bool last,
-                                           bool misplaced, bool active, cudaGraphConditionalHandle next,
-                                           int has_next);
+__device__ __forceinline__ void close_step(const Args<P>& a, const CloseIn& in, unsigned d2, int err, long long left,
+                                           int par, bool init, bool last, bool misplaced, bool active,
+                                           cudaGraphConditionalHandle next, int has_next);
 
 // Force + integration kernel (Sec. 3.1 (c)-(e) of one step and (a) of the
 // next).  A full step: forces f_n, v_n = v_{n-1/2} + f_n dt/2,
@@ -1898,32 +1882,27 @@ __global__ void __launch_bounds__(kB, P::kFp64 ? 3 : 5 * kBlock / kB) k_step(Arg
         }
     }
     if constexpr (!kStepTailNode) {
-        if (last_block_done(C)) close_step<P>(a, err, left, par, init, last, misplaced, active, next, has_next);
+        if (last_block_done(C) && threadIdx.x < 32) {
+            const CloseIn in = read_close_in(C);
+            const unsigned d2 = d2_gather_warp(a);
+            close_step<P>(a, in, d2, err, left, par, init, last, misplaced, active, next, has_next);
+        }
     }
 }
 
 // The step's closing work (Sec. 3.1 (b) for the next step): error bits,
 // counters, the rebuild decision and the shell reach, and in a graph the
-// next conditional rebuild node.  Every lane of warp 0 of one block calls
-// it after all of the step's blocks have finished.
+// next conditional rebuild node.  Lane 0 of one warp does it after all of
+// the step's blocks have finished, from the counters in `in` (read_close_in)
+// and the step's largest squared displacement d2 (d2_gather_warp).
 template <class P>
-__device__ __forceinline__ void close_step(const Args<P>& a, int err, long long left, int par, bool init, bool last,
-                                           bool misplaced, bool active, cudaGraphConditionalHandle next,
-                                           int has_next) {
+__device__ __forceinline__ void close_step(const Args<P>& a, const CloseIn& in, unsigned d2, int err, long long left,
+                                           int par, bool init, bool last, bool misplaced, bool active,
+                                           cudaGraphConditionalHandle next, int has_next) {
     Counters* C = a.ctr;
-    // the counters read here go out together (one round trip to L2 on the
-    // step's serial tail)
-    int err0 = 0, close0 = 0;
-    unsigned far0 = 0u;
-    long long step0 = 0, since0 = 0;
-    if (threadIdx.x == 0) {
-        err0 = C->error;
-        close0 = C->close_flag;
-        far0 = C->far_flag;
-        step0 = C->step;
-        since0 = C->since_reorder;
-    }
-    const unsigned d2 = threadIdx.x < 32 ? d2_gather_warp(a) : 0u;
+    const int err0 = in.err, close0 = in.close;
+    const unsigned far0 = in.far;
+    const long long step0 = in.step, since0 = in.since;
     if (threadIdx.x == 0) {
         int need = 0;
         int errn = err0;
@@ -1962,15 +1941,15 @@ __device__ __forceinline__ void close_step(const Args<P>& a, int err, long long 
 template <class P, bool kFinal>
 __global__ void k_step_tail(Args<P> a, int mode, cudaGraphConditionalHandle next, int has_next) {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
-    Counters* C = a.ctr;
-    const int err = __ldcg(&C->error);
-    const long long left = __ldcg(&C->steps_left);
-    const int par = __ldcg(&C->parity);
+    // every counter and displacement bucket is requested at once: the
+    // kernel is one round trip to L2 and the writes
+    const CloseIn in = read_close_in(a.ctr);
+    const unsigned d2 = d2_gather_warp(a);
     const bool init = kFinal && (mode == kModeInit);
-    const bool last = kFinal && !init && left == 1;
-    const bool misplaced = !kFinal && left == 1;
-    const bool active = init || (err == 0 && left > 0 && !misplaced);
-    close_step<P>(a, err, left, par, init, last, misplaced, active, next, has_next);
+    const bool last = kFinal && !init && in.left == 1;
+    const bool misplaced = !kFinal && in.left == 1;
+    const bool active = init || (in.err == 0 && in.left > 0 && !misplaced);
+    close_step<P>(a, in, d2, in.err, in.left, in.par, init, last, misplaced, active, next, has_next);
 }
 
 // Profiling aid, not part of a step: adds to ctr->list_reads the number of
@@ -2505,8 +2484,6 @@ KernelTable<P> make_kernel_table() {
     KernelTable<P> t;
     t.set_state = (void*)k_set_state<P>;
     t.bin = (void*)k_bin<P>;
-    t.scan_tiles = (void*)k_scan_tiles<P>;
-    t.scan_top = (void*)k_scan_top<P>;
     t.scan_apply = (void*)k_scan_apply<P>;
     t.scatter = (void*)k_scatter<P>;
     t.cellsort = (void*)k_cellsort<P>;

@@ -9,8 +9,6 @@ template <class P>
 struct KernelTable {
     void* set_state;
     void* bin;
-    void* scan_tiles;
-    void* scan_top;
     void* scan_apply;
     void* scatter;
     void* cellsort;

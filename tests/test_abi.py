@@ -130,15 +130,20 @@ def test_plan_bytes_include_the_shell_bin_counts(libmd):
         p = md.md_default_params()
         p.precision = prec
         p.nbr_capacity = 48
-        b1 = md.md_plan(box, 4000, md.WCA_RC, 0.4, 0.005, p).device_bytes
-        b2 = md.md_plan(box, 8000, md.WCA_RC, 0.4, 0.005, p).device_bytes
-        per_atom = (b2 - b1) / 4000
+        # powers of two: the pair buffers hold n rounded up to one
+        b1 = md.md_plan(box, 4096, md.WCA_RC, 0.4, 0.005, p).device_bytes
+        b2 = md.md_plan(box, 8192, md.WCA_RC, 0.4, 0.005, p).device_bytes
+        per_atom = (b2 - b1) / 4096
         real = 8 if prec == md.MD_PREC_FP64 else 4
         pos4 = 32 if prec == md.MD_PREC_FP64 else 16
         state = 3 * 4 + 3 * real + 24 + 3 * real + 3 * real + 2 * pos4 + 16 + 8 + 3 * real + 24 + 3 * real
         # order, nn, lim, io, list; the per-block energy partials add 24 B
         # per 256 atoms
         assert per_atom == pytest.approx(state + 4 + 4 + 7 + 48 + 48 * 4 + 24 / 256, abs=0.01)
+        # between powers of two the two pair buffers are padded to the next
+        # one (the list columns and energy partials round up by a few KB)
+        b3 = md.md_plan(box, 5000, md.WCA_RC, 0.4, 0.005, p).device_bytes
+        assert b3 - (b1 + per_atom * 904) == pytest.approx(2 * pos4 * (8192 - 5000), abs=5000)
 
 
 def test_ensemble_replica_bytes_needs_no_gpu(libmd):
