@@ -242,7 +242,11 @@ struct Sim : SimBase {
     // the neighbour-list build: a block of kWcThreads per x slice of a
     // pencil (a warp per cell), or a thread per cell-ordered atom
     bool warp_build() const { return use_warp_build(prm); }
-    void* build_fn() const { return warp_build() ? kt.build_wc : (a.list_rows ? kt.build_rows : kt.build); }
+    void* build_fn() const {
+        if (warp_build()) return kt.build_wc;
+        if (a.list_rows) return kt.build_rows;
+        return use_direct_build(box, a.n, plan.rn) ? kt.build_direct : kt.build;
+    }
     unsigned grid_build() const {
         return warp_build() ? (unsigned)wc_slices(a) : (unsigned)((a.n + kBuildBlock - 1) / kBuildBlock);
     }

@@ -1168,7 +1168,46 @@ __device__ __noinline__ int build_all(const Args<P>& a, int64_t s) {
     return m;
 }
 
-template <class P, bool kSort, bool kRows, int K>
+// The direct build's second pass, run only for an atom that met a
+// candidate in the band: the band candidates (same FP32 distance as the
+// first pass), decided by the exact FP64 criterion and appended after the m
+// entries already written.  Returns the new count.
+template <class P, bool kRows>
+__device__ __noinline__ int build_band(const Args<P>& a, int64_t s, int m) {
+    const float4 ci = a.cand[s];
+    const int i = __float_as_int(ci.w);
+    int cx, cy, cz;
+    unpack_cell(a.cell[i], cx, cy, cz);
+    constexpr int cs = kRows ? 1 : 32;
+    int* col = a.nbr + (kRows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31));
+    const int cap = a.cap, n = (int)a.n;
+    for (int d = 0; d < 27; d++) {
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const int c = cell_index(wrap_add(cx, dx, a.G[0]), wrap_add(cy, dy, a.G[1]), wrap_add(cz, dz, a.G[2]), a.G);
+        const int end = min(a.cell_start[c + 1], n);
+        const unsigned code = (unsigned)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4));
+        for (int t = a.cell_start[c]; t < end; t++) {
+            const float4 pj = __ldg(a.cand + t);
+            const float ex = (ci.x - (float)dx * a.wf[0]) - pj.x;
+            const float ey = (ci.y - (float)dy * a.wf[1]) - pj.y;
+            const float ez = (ci.z - (float)dz * a.wf[2]) - pj.z;
+            const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            if (!(rr >= a.rn2_lo && rr < a.rn2_hi) || t == (int)s) continue;
+            const int j = __float_as_int(pj.w);
+            if (!within_rn_fp64(a, i, j, code)) continue;
+            if (m < cap) col[(size_t)m * cs] = j | (int)(code << kCodeShift);
+            m++;
+        }
+    }
+    return m;
+}
+
+// kDirect: the direct form for lists longer than the stage (dense or long-
+// range workloads): each accepted entry goes straight to the list, in order
+// of discovery, with a lim of "all entries"; a candidate in the band only
+// marks the atom, and build_band decides the marked atom's band candidates
+// afterwards (the rare FP64 path then costs the scan loop no registers).
+template <class P, bool kSort, bool kRows, int K, bool kDirect = false>
 __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* stage, int stride) {
     Counters* C = a.ctr;
     int m = 0;  // staged candidates (FP32 r^2 < rn2_hi)
@@ -1179,7 +1218,8 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
     constexpr int cs = kRows ? 1 : 32;
     int* col = a.nbr + (kRows ? (size_t)i * (size_t)a.cap : ((size_t)(i >> 5) * (size_t)a.cap) * 32 + (i & 31));
     const int cap = a.cap, n = (int)a.n, self = (int)s;
-    const float hi2 = a.rn2_hi;
+    const float hi2 = a.rn2_hi, lo2d = a.rn2_lo;
+    bool unsure = false;  // (direct form) a candidate in the band was met
     const int xs[3] = {wrap_add(cx, -1, a.G[0]), cx, wrap_add(cx, 1, a.G[0])};
     const float qxs[3] = {ci.x + a.wf[0], ci.x, ci.x - a.wf[0]};  // x seen from cells x-1, x, x+1
     // candidate ranges of the three cells of row r = (d_y + 1) + 3 (d_z + 1)
@@ -1208,8 +1248,15 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
             const float ey = qy - pj.y;
             const float ez = qz - pj.z;
             const float rr = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            if (m < K) stage[m * stride] = make_int2(__float_as_int(pj.w) | code, __float_as_int(rr));
-            m += (rr < hi2 && t != self) ? 1 : 0;
+            if constexpr (kDirect) {
+                const bool take = rr < lo2d && t != self;
+                unsure |= !(rr < lo2d) && rr < hi2;
+                if (take && m < cap) col[(size_t)m * cs] = __float_as_int(pj.w) | code;
+                m += take ? 1 : 0;
+            } else {
+                if (m < K) stage[m * stride] = make_int2(__float_as_int(pj.w) | code, __float_as_int(rr));
+                m += (rr < hi2 && t != self) ? 1 : 0;
+            }
         };
 #pragma unroll
         for (int k = 0; k < 3; k++) {
@@ -1233,7 +1280,14 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
             row_bounds(r + 1, lo, hi);
         }
     }
-    if (m > K) {  // rare: too long for the stage
+    if constexpr (kDirect) {
+        if (unsure) m = build_band<P, kRows>(a, s, m);
+        a.nn[i] = m < cap ? m : cap;
+        if constexpr (kSort) {
+#pragma unroll
+            for (int k = 1; k < kShellBins; k++) a.lim[(size_t)(k - 1) * a.n + i] = 255;
+        }
+    } else if (m > K) {  // rare: too long for the stage
         m = build_all<P, kRows>(a, s);
         const int kept = m < cap ? m : cap;
         a.nn[i] = kept;
@@ -1291,21 +1345,21 @@ __device__ __forceinline__ int build_item_t(const Args<P>& a, int64_t s, int2* s
 }
 
 // K: the stage depth (8-byte words per thread at stage[t * stride]).
-template <class P, bool kRows = false, int K = kBuildStage>
+template <class P, bool kRows = false, int K = kBuildStage, bool kDirect = false>
 __device__ __forceinline__ int build_item(const Args<P>& a, int64_t s, int2* stage, int stride) {
-    return a.shell_bins ? build_item_t<P, true, kRows, K>(a, s, stage, stride)
-                        : build_item_t<P, false, kRows, K>(a, s, stage, stride);
+    return a.shell_bins ? build_item_t<P, true, kRows, K, kDirect>(a, s, stage, stride)
+                        : build_item_t<P, false, kRows, K, kDirect>(a, s, stage, stride);
 }
 
-template <class P, bool kRows = false>
+template <class P, bool kRows = false, bool kDirect = false>
 __global__ void __launch_bounds__(kBuildBlock, 8) k_build(Args<P> a, int guard) {
     constexpr int kWarps = kBuildBlock / 32;
     __shared__ int s_max[kWarps], s_sum[kWarps];
-    __shared__ int2 s_stage[kBuildStage * kBuildBlock];
+    __shared__ int2 s_stage[kDirect ? 1 : kBuildStage * kBuildBlock];
     Counters* C = a.ctr;
     if (guard && !C->rebuild_flag) return;
     const int64_t s = gtid();
-    const int m = s < a.n ? build_item<P, kRows>(a, s, s_stage + threadIdx.x, kBuildBlock) : 0;
+    const int m = s < a.n ? build_item<P, kRows, kBuildStage, kDirect>(a, s, s_stage + threadIdx.x, kBuildBlock) : 0;
     // block maximum and sum of the list lengths (m <= 512, so the block's
     // sum fits an int)
     int bm = m, bs = m;
@@ -2491,6 +2545,7 @@ KernelTable<P> make_kernel_table() {
     t.commit = (void*)k_commit<P>;
     t.build = (void*)k_build<P>;
     t.build_rows = (void*)k_build<P, true>;
+    t.build_direct = (void*)k_build<P, false, true>;
     t.build_wc = (void*)k_build_wc<P>;
     t.rebuild_done = (void*)k_rebuild_done<P>;
     t.cond = (void*)k_cond<P>;

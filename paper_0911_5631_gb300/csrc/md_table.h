@@ -16,6 +16,7 @@ struct KernelTable {
     void* commit;
     void* build;     // thread per atom
     void* build_rows;  // the same, lists with each atom's entries contiguous (W transposed)
+    void* build_direct;  // the same for lists longer than its stage: entries written as found
     void* build_wc;  // warp per home cell (warp-cooperative)
     void* rebuild_done;
     void* cond;

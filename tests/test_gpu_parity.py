@@ -116,6 +116,66 @@ def test_rebuilds_along_trajectory_match_oracle(case, prec, build):
     s.close()
 
 
+def _clustered_state(seed=7):
+    """A dense FCC block (rho 2.1: 42 neighbours within r_n) inside a dilute
+    FCC lattice (rho 0.5), both slightly jittered: a low mean density with a
+    few atoms whose lists are far longer than the mean."""
+    rng = np.random.default_rng(seed)
+    basis = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]])
+    def fcc(cells, a):
+        g = np.stack(np.meshgrid(*[np.arange(cells)] * 3, indexing="ij"), -1).reshape(-1, 1, 3)
+        return ((g + basis[None]) * a).reshape(-1, 3)
+    L = np.array([16.0, 16.0, 16.0])
+    dilute = fcc(8, 2.0) - 8.0 + 0.5
+    a_d = (4 / 2.1) ** (1 / 3)
+    dense = fcc(4, a_d) - 2.0 * a_d
+    side = 4 * a_d
+    keep = np.any(np.abs(dilute + 0.25 * a_d) > side / 2 + 0.8, axis=1)
+    pos = np.concatenate([dilute[keep], dense]) + rng.normal(0, 0.01, (keep.sum() + len(dense), 3))
+    vel = rng.normal(0, 1.0, pos.shape)
+    return pos, vel, L
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_thread_build_forms_match_oracle(prec):
+    # The thread-per-atom build stages up to 20 candidates per atom; an atom
+    # with more is scanned a second time and written unsorted (the dense
+    # block of a clustered state).  A workload whose expected list comes
+    # near the stage depth takes the direct form, which writes entries as it
+    # finds them (skin 1.0: about 32 entries per atom), checked at the load
+    # and at in-trajectory rebuilds of a melted state.
+    pos, vel, L = _clustered_state()
+    s = sim(pos, vel, L, skin=0.4, precision=prec)
+    p, _ = s.get_state()
+    rn = RC + 0.4
+    pairs, entries = s.neighbor_pairs()
+    assert entries == 2 * len(pairs)
+    assert_same_pairs(pairs, oracle.pairs_cells(p, L, oracle_grid(L, rn), rn), p, L, rn)
+    assert s.measure()["max_neighbors"] > 20
+    s.close()
+    case = (2048, 0.8, 1.0, 1.0, 0.15, (1, 1, 1), 6)
+    s, pos, vel, L, skin = _setup(case, prec)
+    p, _ = s.get_state()
+    rn = RC + skin
+    pairs, entries = s.neighbor_pairs()
+    assert entries == 2 * len(pairs)
+    assert_same_pairs(pairs, oracle.pairs_cells(p, L, oracle_grid(L, rn), rn), p, L, rn)
+    s.close()
+    pos, vel, L, skin = _fluid(case)
+    s = sim(pos, vel, L, skin=skin, precision=prec, reorder_interval=15)
+    G = np.array(s.plan()["G"])
+    seen, last, steps = 0, s.measure()["rebuilds"], 0
+    while seen < 2 and steps < 400:
+        s.step(1)
+        steps += 1
+        if s.measure()["rebuilds"] > last:
+            last = s.measure()["rebuilds"]
+            seen += 1
+            _check_rebuilt_state(s, L, skin, G)
+    assert seen == 2
+    s.close()
+
+
 @pytest.mark.parametrize("case", CASES, ids=IDS)
 def test_pair_sets_identical_across_precisions(case):
     a = _setup(case, "mixed")[0]
