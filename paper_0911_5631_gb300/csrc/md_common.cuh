@@ -30,10 +30,10 @@ constexpr int kStageRows = 12;  // neighbour-list rows a step-kernel warp copies
 // r_c.  The build stages up to kBuildStage candidates per atom in shared
 // memory.
 constexpr int kShellBins = 8;
-constexpr int kBuildStage = 20;
+constexpr int kBuildStage = 18;
 // Threads per block of the thread-per-atom build (its stage: kBuildStage
-// 8-byte words per thread in shared memory; 20 measured best at the 1M-atom
-// workload, against 16, 24 and 32).
+// 8-byte words per thread in shared memory; 18 measured best at the 1M-atom
+// workload, against 16, 20, 24 and 32).
 constexpr int kBuildBlock = 128;
 // The build's candidate loop issues kBuildUnroll loads before it uses them,
 // and the cell ranges of the next (c_y, c_z) row are loaded while a row runs.

@@ -103,11 +103,13 @@ inline bool use_warp_build(const md_params& p) { return p.build_kernel == MD_BUI
 
 // Whether the thread-per-atom build writes entries as it finds them rather
 // than staging them for the shell-bin sort: when the expected number of
-// entries per atom (the density times the r_n sphere) comes near the stage
-// depth, most atoms would overflow the stage and be scanned twice.
+// entries per atom (the density times the r_n sphere) exceeds the stage
+// depth, most atoms would overflow the stage and be scanned twice.  (Below
+// it, the few atoms that overflow are scanned twice and keep the shell-bin
+// savings of the rest.)
 inline bool use_direct_build(const double box[3], int64_t n, double rn) {
     const double nbar = 4.0 / 3.0 * M_PI * rn * rn * rn * (double)n / (box[0] * box[1] * box[2]);
-    return nbar > 0.75 * kBuildStage;
+    return nbar > kBuildStage;
 }
 
 // Scalar members of Args from a plan.
