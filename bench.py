@@ -106,11 +106,37 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(text):
+    """C++ source without comments, whitespace runs collapsed: a comment edit
+    leaves the compiled kernels, and so the hash, unchanged."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":  # string or character literal, kept whole
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash():
+    """Hash of the kernel source (code only) that the committed ncu
+    summaries name in their `kernel_source` line."""
     h = hashlib.sha256()
     for f in ("md_kernels.cuh", "md_common.cuh"):
-        with open(os.path.join(ROOT, "paper_0911_5631_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_0911_5631_gb300", "csrc", f), encoding="utf-8") as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

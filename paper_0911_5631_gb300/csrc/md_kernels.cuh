@@ -1128,8 +1128,8 @@ __device__ __forceinline__ int shell_reach(const Args<P>& a, unsigned d2bits) {
 // overwritten by the next one), so that a candidate costs its distance, one
 // store and no branch.  The loop issues kBuildUnroll candidate loads before
 // it uses them (loads past a cell's end are predicated off) and loads the
-// next row's cell ranges while a row runs: the loop is bound by the latency
-// of those L1 hits, not by its instructions.  Afterwards the staged band
+// next row's cell ranges while a row runs, to hide the latency of those L1
+// hits (without them the loop was latency-bound).  Afterwards the staged band
 // entries get the FP64 test (rare), the survivors are written out ordered
 // by shell bin (a counting sort whose bin counts sit in the bytes of one
 // 64-bit word) and lim receives the number of entries below each bin

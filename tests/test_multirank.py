@@ -45,3 +45,15 @@ def test_single_rank_aggregation():
     import bench
     value, ms = bench.job_throughput(500.0, 20.0)
     assert ms == 20.0 and value == pytest.approx(25000.0)
+
+
+def test_kernel_source_hash_ignores_comments_and_whitespace():
+    # the ncu summaries name the kernel source they were taken on by this
+    # hash; a comment or layout edit must keep it, a code edit must change it
+    import bench
+    code = 'int a = 1;  // one\n/* two\n */ const char* s = "x // y";\nchar q = \'/\';'
+    same = "int a = 1;\n\n const char* s = \"x // y\"; /* note */ char q = '/';"
+    other = 'int a = 2; const char* s = "x // y"; char q = \'/\';'
+    assert bench._code_only(code) == bench._code_only(same)
+    assert bench._code_only(code) != bench._code_only(other)
+    assert '"x // y"' in bench._code_only(code)
