@@ -90,8 +90,9 @@ inline int resolve_plan(const double box[3], int64_t n, double rc, double skin, 
                        3 * real_b /*scratch*/ +
                        4 /*order*/ + 4 /*nn*/ + (kShellBins - 1) /*lim*/ + 48 /*io*/;
     int64_t ncol = (n + 31) / 32 * 32;
-    out->device_bytes = per_atom * n + 2 * pos4_b * (pair_slots(n) - n) + ncol * cap * 4 + (2 * nc + 1) * 4 + ((nc + kScanTile - 1) / kScanTile) * 4 +
-                        3 * nb * 8 + (int64_t)sizeof(Counters) + kD2Buckets * 32 * 4;
+    out->device_bytes = per_atom * n + 2 * pos4_b * (pair_slots(n) - n) /*pair buffers padded*/ + ncol * cap * 4 +
+                        (2 * nc + 1) * 4 + ((nc + kScanTile - 1) / kScanTile) * 4 + 3 * nb * 8 +
+                        (int64_t)sizeof(Counters) + kD2Buckets * 32 * 4;
     return MD_OK;
 }
 
