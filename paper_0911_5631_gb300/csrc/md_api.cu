@@ -360,30 +360,39 @@ struct Sim : SimBase {
         return MD_OK;
     }
 
+    // K steps: k_cond, then per step the step kernel and its closing kernel,
+    // with a conditional rebuild node before every m-th step (every step in
+    // the cell-list-only form, which rebuilds at each).  The closing kernel
+    // before a conditional node sets its handle; a step after another whose
+    // rebuild is due waits for the next conditional node.
     int build_chunk(Chunk& c, int K) {
         MD_CUDA(cudaGraphCreate(&c.g, 0));
-        std::vector<cudaGraphConditionalHandle> h(K);
-        for (int s = 0; s < K; s++) MD_CUDA(cudaGraphConditionalHandleCreate(&h[s], c.g, 0, 0));
+        const int m = (prm.cell_list_only || a.n > kRebuildEveryMaxAtoms) ? 1 : kRebuildEvery;
+        std::vector<cudaGraphConditionalHandle> h((K + m - 1) / m);
+        for (auto& hh : h) MD_CUDA(cudaGraphConditionalHandleCreate(&hh, c.g, 0, 0));
         cudaGraphNode_t prev = nullptr, node = nullptr;
         MD_CUDA(add_kernel(c.g, nullptr, &node, kt.cond, 1, 32, a, h[0]));
         prev = node;
         int mode = kModeAuto;
         for (int s = 0; s < K; s++) {
-            NodeParams buf;
-            cudaGraphNodeParams& cp = buf.get();
-            cp.type = cudaGraphNodeTypeConditional;
-            cp.conditional.handle = h[s];
-            cp.conditional.type = cudaGraphCondTypeIf;
-            cp.conditional.size = 1;
-            cudaGraphNode_t ifn = nullptr;
-            MD_CUDA(cudaGraphAddNode(&ifn, c.g, &prev, nullptr, 1, &cp));
-            int r = build_body(cp.conditional.phGraph_out[0]);
-            if (r) return r;
-            cudaGraphConditionalHandle nxt = (s + 1 < K) ? h[s + 1] : 0;
-            int has = (s + 1 < K) ? 1 : 0;
+            if (s % m == 0) {
+                NodeParams buf;
+                cudaGraphNodeParams& cp = buf.get();
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = h[s / m];
+                cp.conditional.type = cudaGraphCondTypeIf;
+                cp.conditional.size = 1;
+                cudaGraphNode_t ifn = nullptr;
+                MD_CUDA(cudaGraphAddNode(&ifn, c.g, &prev, nullptr, 1, &cp));
+                int r = build_body(cp.conditional.phGraph_out[0]);
+                if (r) return r;
+                prev = ifn;
+            }
+            const int has = (s + 1 < K && (s + 1) % m == 0) ? 1 : 0;
+            cudaGraphConditionalHandle nxt = has ? h[(s + 1) / m] : 0;
             // only a graph's last node can meet the last step of a call
-            MD_CUDA(add_kernel(c.g, &ifn, &node, step_fn(s + 1 == K), step_grid(s + 1 == K), step_block(s + 1 == K), a,
-                               mode, nxt, has));
+            MD_CUDA(add_kernel(c.g, &prev, &node, step_fn(s + 1 == K), step_grid(s + 1 == K), step_block(s + 1 == K),
+                               a, mode, nxt, has));
             if (kStepTailNode) {
                 cudaGraphNode_t stepn = node;
                 MD_CUDA(add_kernel(c.g, &stepn, &node, tail_fn(s + 1 == K), 1, 32, a, mode, nxt, has));
@@ -531,6 +540,7 @@ struct Sim : SimBase {
     }
 
     int finish_pending(int64_t* steps_left_out) {
+        bool overflowed = false;
         for (int attempt = 0; attempt < 16; attempt++) {
             Counters c;
             int r = read_counters(&c);
@@ -538,6 +548,7 @@ struct Sim : SimBase {
             r = check_fatal(c);
             if (r) return r;
             if (c.error & kErrOverflow) {
+                overflowed = true;
                 r = regrow(c);
                 if (r) return r;
                 // the step that met the overflow has not run yet
@@ -549,11 +560,22 @@ struct Sim : SimBase {
                 if (r) return r;
                 continue;
             }
+            if (c.steps_left > 0 && c.error == 0) {
+                // steps that waited for a rebuild inside a graph: run them
+                // now (each round leaves fewer to wait)
+                r = run_steps(c.steps_left);
+                if (r) return r;
+                continue;
+            }
             if (steps_left_out) *steps_left_out = c.steps_left;
             return MD_OK;
         }
-        err = "neighbour list kept overflowing";
-        return MD_EOVERFLOW;
+        if (overflowed) {
+            err = "neighbour list kept overflowing";
+            return MD_EOVERFLOW;
+        }
+        err = "steps that waited for a rebuild did not complete";
+        return MD_ECUDA;
     }
 
     // ---- API -------------------------------------------------------------

@@ -21,6 +21,15 @@ constexpr bool kStepTailNode = true;
 // Each warp of the step kernel reads the counters itself (no opening block
 // barrier).
 constexpr bool kWarpView = true;
+// A graph evaluates the rebuild condition (a conditional node, about 5 us
+// whether taken or not) before every kRebuildEvery-th step only; a step in
+// between whose rebuild is due waits (does nothing) for the next one, and
+// the call runs the waited steps at its end.  A waiting step still launches
+// its grid, whose cost grows with the system: measured, checking every third
+// step gains 5 % at 1M atoms and loses 1 % at 8M, so systems above
+// kRebuildEveryMaxAtoms check before every step.
+constexpr int kRebuildEvery = 3;
+constexpr int64_t kRebuildEveryMaxAtoms = int64_t(1) << 21;
 constexpr int kStageRows = 12;  // neighbour-list rows a step-kernel warp copies to shared memory
 // The skin shell [r_c, r_n) is cut into kShellBins bins of width skin /
 // kShellBins.  The build sorts each atom's entries by the bin of their

@@ -67,33 +67,38 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// pend: a rebuild is due and has not run (the step's list is stale).
 struct View {
     int err;
     int par;
     long long left;
+    int pend;
 };
 // The same view read by each warp on its own (lane 0 reads, a shuffle
 // spreads it): no block barrier.
 __device__ __forceinline__ View load_view_warp(const Counters* C) {
-    int e = 0, p = 0;
+    int e = 0, p = 0, r = 0;
     long long l = 0;
     if ((threadIdx.x & 31) == 0) {
         e = C->error;
         p = C->parity;
         l = C->steps_left;
+        r = C->rebuild_flag;
     }
-    return View{__shfl_sync(0xffffffffu, e, 0), __shfl_sync(0xffffffffu, p, 0), __shfl_sync(0xffffffffu, l, 0)};
+    return View{__shfl_sync(0xffffffffu, e, 0), __shfl_sync(0xffffffffu, p, 0), __shfl_sync(0xffffffffu, l, 0),
+                __shfl_sync(0xffffffffu, r, 0)};
 }
 __device__ __forceinline__ View load_view(const Counters* C) {
-    __shared__ int s_err, s_par;
+    __shared__ int s_err, s_par, s_pend;
     __shared__ long long s_left;
     if (threadIdx.x == 0) {
         s_err = C->error;
         s_par = C->parity;
         s_left = C->steps_left;
+        s_pend = C->rebuild_flag;
     }
     __syncthreads();
-    return View{s_err, s_par, s_left};
+    return View{s_err, s_par, s_left, s_pend};
 }
 
 // Fixed-shape block sum of kBlock values (result valid in thread 0).
@@ -1835,7 +1840,7 @@ __device__ __forceinline__ void step_atom(const Args<P>& a, int64_t i, bool in, 
 // The counters a step's closing work reads, loaded by lane 0 in one round
 // trip to L2 (other blocks of the step wrote the flags: read past L1).
 struct CloseIn {
-    int err = 0, par = 0, close = 0;
+    int err = 0, par = 0, close = 0, pend = 0;
     unsigned far = 0u;
     long long left = 0, step = 0, since = 0;
 };
@@ -1849,6 +1854,7 @@ __device__ __forceinline__ CloseIn read_close_in(const Counters* C) {
         r.left = __ldcg(&C->steps_left);
         r.step = __ldcg(&C->step);
         r.since = __ldcg(&C->since_reorder);
+        r.pend = __ldcg(&C->rebuild_flag);
     }
     return r;
 }
@@ -1911,7 +1917,10 @@ __global__ void __launch_bounds__(kB, P::kFp64 ? 3 : 5 * kBlock / kB) k_step(Arg
     const bool init = kFinal && (mode == kModeInit);
     const bool last = kFinal && !init && left == 1;
     const bool misplaced = !kFinal && left == 1;  // a plain node must never run a call's last step
-    const bool active = init || (err == 0 && left > 0 && !misplaced);
+    // a step whose rebuild is due but has not run (a graph checks for
+    // rebuilds every kRebuildEvery steps) waits: it does nothing, and the
+    // call runs one step more at its end
+    const bool active = init || (err == 0 && left > 0 && !misplaced && !vw.pend);
     const bool energy = init || last;
     const pos4* pc = par ? a.pB : a.pA;
     pos4* pn = par ? a.pA : a.pB;
@@ -1983,6 +1992,8 @@ __device__ __forceinline__ void close_step(const Args<P>& a, const CloseIn& in, 
         }
         C->d2max = d2;
         C->reach = shell_reach(a, d2);
+        // a step that waited for its rebuild leaves it due
+        if (!active && !init && in.pend && errn == 0) need = 1;
         if (has_next) cudaGraphSetConditional(next, need ? 1u : 0u);
         C->ticket = 0;
     }
@@ -2002,7 +2013,7 @@ __global__ void k_step_tail(Args<P> a, int mode, cudaGraphConditionalHandle next
     const bool init = kFinal && (mode == kModeInit);
     const bool last = kFinal && !init && in.left == 1;
     const bool misplaced = !kFinal && in.left == 1;
-    const bool active = init || (in.err == 0 && in.left > 0 && !misplaced);
+    const bool active = init || (in.err == 0 && in.left > 0 && !misplaced && !in.pend);
     close_step<P>(a, in, d2, in.err, in.left, in.par, init, last, misplaced, active, next, has_next);
 }
 
