@@ -43,6 +43,32 @@ def test_graphs_and_stream_launches_agree_bitwise(prec):
         assert np.array_equal(x, y)
 
 
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_steps_waiting_for_a_rebuild_are_completed(prec):
+    # A graph checks for a rebuild before every third step; a step whose
+    # rebuild is due in between waits, and md_step runs the waited steps at
+    # its end.  A hot fluid with a thin skin rebuilds every few steps, so
+    # waits are frequent: every call must still end after exactly its steps,
+    # with the trajectory and the rebuilds of stream launches.
+    pos, vel, L = state(2048, 0.8, 2.5, 21)
+    out = []
+    for graphs in (True, False):
+        s = sim(pos, vel, L, skin=0.15, precision=prec, use_graphs=graphs)
+        done, counts = 0, []
+        for k in (37, 1, 64, 5, 100):
+            s.step(k)
+            done += k
+            m = s.measure()
+            assert m["step"] == done
+            counts.append(m["rebuilds"])
+        p, v = s.get_state()
+        out.append((p, v, s.forces(), counts))
+        s.close()
+    assert out[0][3] == out[1][3] and out[0][3][-1] > 40
+    for x, y in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(x, y)
+
+
 def test_mixed_trajectory_independent_of_reordering():
     # int64 force sums make every atom's result independent of storage order
     ref = _run("mixed", reorder_interval=0)
