@@ -78,8 +78,10 @@ typedef struct md_params {
                                  from density and r_n.  Grown automatically.   */
     int32_t use_graphs;       /* 1 (default): md_step replays CUDA graphs whose
                                  rebuild branch is a device-side conditional
-                                 node; 0: plain stream launches (same results,
-                                 bit for bit).                                 */
+                                 node (checked every third step; a step whose
+                                 rebuild is due in between waits and runs
+                                 before md_step returns); 0: plain stream
+                                 launches (same results, bit for bit).         */
     int32_t device;           /* CUDA device ordinal; -1 (default) = current   */
     int32_t shell_bins;       /* 1 (default): the build sorts each atom's list
                                  by distance, and a step reads only the entries

@@ -3,11 +3,13 @@
 // A handle owns the device state of one simulation and a CUDA stream.  One
 // md_step call enqueues: the half kick + drift of the first step, then the
 // steps themselves.  With graphs enabled the steps run as replays of a
-// CUDA graph holding K (conditional rebuild, force + integrate) pairs; the
-// step kernel decides on the device whether the next rebuild branch runs
-// (cudaGraphSetConditional), so no host round trip sits inside the loop.
-// Without graphs the same kernels are launched one by one and the rebuild
-// kernels return early when the device flag is clear.
+// CUDA graph holding K (force + integrate, closing) pairs with a conditional
+// rebuild node before every third step; the closing kernel decides on the
+// device whether the next rebuild branch runs (cudaGraphSetConditional), so
+// no host round trip sits inside the loop, and a step whose rebuild is due
+// before the next conditional node waits (the call runs it at its end).
+// Without graphs the same kernels are launched one by one and the host
+// reads the rebuild flag before each step.
 #include <cuda_runtime.h>
 
 #include <cmath>

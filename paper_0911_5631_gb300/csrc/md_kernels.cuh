@@ -1870,8 +1870,11 @@ __device__ __forceinline__ void close_step(const Args<P>& a, const CloseIn& in, 
 // and the skin/2 test.  The kFinal variant also handles the last step of an
 // md_step call (forces, v_n, PE/W/KE partials, no drift) and mode
 // kModeInit (forces of a freshly loaded state); the plain variant, used for
-// every other step, carries no energy accumulators.  The last block
-// advances the counters and, in a graph, sets the next conditional rebuild.
+// every other step, carries no energy accumulators.  The closing work
+// (counters, the rebuild decision, in a graph the next conditional rebuild)
+// runs in k_step_tail, or with kStepTailNode off in the last block.  A step
+// whose rebuild is due and has not run (a graph checks every
+// kRebuildEvery steps) does nothing.
 //
 // The template arguments after kFinal select the kernel variants of the
 // paper's ablations (mixed list form): kB threads per block (Table 6),
