@@ -31,6 +31,11 @@ constexpr bool kWarpView = true;
 constexpr int kRebuildEvery = 3;
 constexpr int64_t kRebuildEveryMaxAtoms = int64_t(1) << 21;
 constexpr int kStageRows = 12;  // neighbour-list rows a step-kernel warp copies to shared memory
+// The force loop reads the staged rows four at a time (the reads are not
+// predicated, only the gathers they feed), so the staged count -- the
+// smaller of kStageRows and the list capacity, itself rounded up to a
+// multiple of 4 -- must be a multiple of 4 to stay inside the warp's rows.
+static_assert(kStageRows % 4 == 0, "kStageRows must be a multiple of 4");
 // The skin shell [r_c, r_n) is cut into kShellBins bins of width skin /
 // kShellBins.  The build sorts each atom's entries by the bin of their
 // distance at the build and records, for k = 1 .. kShellBins, how many

@@ -75,7 +75,7 @@ inline int resolve_plan(const double box[3], int64_t n, double rc, double skin, 
             double nbar = 4.0 / 3.0 * M_PI * rn * rn * rn * rho;
             cap = (int)std::ceil(nbar + 6.0 * std::sqrt(nbar) + 8.0);
         }
-        cap = (cap + 3) & ~3;
+        cap = (cap + 3) & ~3;  // a multiple of 4 (the step kernel reads its staged rows four at a time)
         if (cap < 8) cap = 8;
         int cap_max = p->precision == MD_PREC_MIXED ? md::kMaxCapMixed : 4096;
         if (cap > cap_max) cap = cap_max;
