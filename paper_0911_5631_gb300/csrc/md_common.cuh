@@ -45,6 +45,9 @@ static_assert(kStageRows % 4 == 0, "kStageRows must be a multiple of 4");
 // memory.
 constexpr int kShellBins = 8;
 constexpr int kBuildStage = 18;
+// The build's bin counts sit in the bytes of one 64-bit word: eight bins,
+// and no count above 255.
+static_assert(kShellBins == 8 && kBuildStage < 256, "one byte per shell bin in a 64-bit word");
 // Threads per block of the thread-per-atom build (its stage: kBuildStage
 // 8-byte words per thread in shared memory; 18 measured best at the 1M-atom
 // workload, against 16, 20, 24 and 32).
@@ -65,6 +68,7 @@ constexpr int kD2Buckets = 64;
 // one sends too many atoms of its denser replicas to the rescan (measured
 // at the 512-replica workload: 16 beats 12, 14, 20 and 24).
 constexpr int kEnsBuildStage = 16;
+static_assert(kEnsBuildStage < 256, "one byte per shell bin in a 64-bit word");
 constexpr int kEnsSmemInts = kStageRows > 2 * kEnsBuildStage ? kStageRows : 2 * kEnsBuildStage;
 // Elements per block of the cell-count scan (kBlock threads x 8).
 constexpr int kScanTile = 2048;
